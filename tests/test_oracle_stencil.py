@@ -1,0 +1,190 @@
+"""Pins of the oracle's finite-difference operators against what the paper
+and the mathematics fix (Sec. 2.2, App. A).  CPU only."""
+from fractions import Fraction as Fr
+
+import numpy as np
+import pytest
+
+from oracle import stencil
+
+PARAMS = [(stencil.M47_SMC, stencil.M48_SMC), (stencil.M47_ZERO, stencil.M48_ZERO),
+          (stencil.M47_OPT, stencil.M48_OPT), (Fr(1, 7), Fr(-3, 11))]
+
+
+def apply_exact(M, a, u, x0):
+    """(H_{x0+1/2} - H_{x0-1/2}) at h = 1 in exact rationals (eqs. DaDu, H)."""
+    s = len(M) // 2
+
+    def H(i):
+        return sum(a(i + m - s + 1) * M[m][n] * u(i + n - s + 1)
+                   for m in range(2 * s) for n in range(2 * s) if M[m][n] != 0)
+    return H(x0) - H(x0 - 1)
+
+
+def exact_second(p, q, x):
+    """(x^p (x^q)')' at x."""
+    if q == 0 or p + q < 2:
+        return Fr(0)
+    return Fr(q * (p + q - 1)) * Fr(x) ** (p + q - 2)
+
+
+@pytest.mark.parametrize("m47,m48", PARAMS)
+def test_narrow8_exact_to_degree_9(m47, m48):
+    """The 8th-order narrow stencil is exact whenever deg a + deg u <= 9, for
+    every choice of the two free parameters (Sec. 2.2)."""
+    M = stencil.narrow8_exact(m47, m48)
+    for p in range(10):
+        for q in range(10 - p):
+            for x0 in (0, 2, -3):
+                got = apply_exact(M, lambda x: Fr(x) ** p, lambda x: Fr(x) ** q, x0)
+                assert got == exact_second(p, q, x0), (p, q, x0)
+
+
+def truncation_coefficients(m47, m48):
+    """Coefficients of a^(j) u^(10-j), j = 0..9, in the App. A error formula."""
+    return [Fr(-1, 3150), Fr(-1, 630), Fr(-1, 35), Fr(-113, 840) - 4 * m48,
+            Fr(-487, 1680) - 14 * m48,
+            Fr(-4513, 12600) + Fr(2, 5) * m47 - Fr(92, 5) * m48,
+            Fr(-2777, 10080) + m47 - 11 * m48,
+            Fr(-3181, 25200) + Fr(4, 5) * m47 - Fr(14, 5) * m48,
+            Fr(-1403, 50400) + Fr(1, 5) * m47 - Fr(1, 5) * m48, Fr(-1, 630)]
+
+
+def falling(n, k):
+    out = 1
+    for i in range(k):
+        out *= (n - i)
+    return out
+
+
+@pytest.mark.parametrize("m47,m48", PARAMS)
+def test_narrow8_truncation_error_matches_appendix(m47, m48):
+    """For deg a + deg u = 10 the discrete error is exactly the h^8 term of the
+    appendix formula (higher terms need 12 derivatives)."""
+    M = stencil.narrow8_exact(m47, m48)
+    C = truncation_coefficients(Fr(m47), Fr(m48))
+    for p in range(11):
+        q = 10 - p
+        for x0 in (0, 1, -2):
+            got = apply_exact(M, lambda x: Fr(x) ** p, lambda x: Fr(x) ** q, x0) \
+                - exact_second(p, q, x0)
+            want = Fr(0)
+            for j in range(10):
+                if j <= p and 10 - j <= q:
+                    aj = falling(p, j) * Fr(x0) ** (p - j)
+                    uj = falling(q, 10 - j) * Fr(x0) ** (q - 10 + j)
+                    want += C[j] * aj * uj
+            assert got == want, (p, q, x0)
+
+
+def test_narrow8_rows_sum_to_zero_and_antisymmetry():
+    M = stencil.narrow8_exact()
+    for r in range(8):
+        assert sum(M[r]) == 0
+        for c in range(8):
+            assert M[7 - r][7 - c] == -M[r][c]
+
+
+def test_narrow8_constant_coefficient_is_standard_second_derivative():
+    """With a = 1 the stencil collapses to the 9-point 8th-order second
+    derivative [-1/560, 8/315, -1/5, 8/5, -205/72, ...]."""
+    for m47, m48 in PARAMS:
+        M = stencil.narrow8_exact(m47, m48)
+        w = []
+        for j in range(-4, 5):
+            w.append(apply_exact(M, lambda x: Fr(1), lambda x, j=j: Fr(1 if x == j else 0), 0))
+        assert w == [Fr(-1, 560), Fr(8, 315), Fr(-1, 5), Fr(8, 5), Fr(-205, 72),
+                     Fr(8, 5), Fr(-1, 5), Fr(8, 315), Fr(-1, 560)]
+
+
+def test_nyquist_damping_narrow_vs_wide():
+    """Narrow symbol at k = pi is strictly negative (-6.5016/h^2); the wide
+    D(D u) symbol there is exactly 0 (Sec. 1)."""
+    N = 32
+    u = np.array([(-1.0) ** j for j in range(N)])
+    a = np.ones(N)
+    M = stencil.to_float(stencil.narrow8_exact())
+    lu = stencil.narrow(np.pad(a, 4, mode="wrap"), np.pad(u, 4, mode="wrap"), 0, 1.0, M)
+    sym = lu / u
+    assert np.allclose(sym, -(2 * (8 / 5 + 8 / 315) + 2 * (1 / 5 + 1 / 560) + 205 / 72))
+    assert abs(sym[0] + 6.501587301587301) < 1e-12
+    wd = stencil.wide(np.pad(a, 8, mode="wrap"), np.pad(u, 8, mode="wrap"), 0, 1.0)
+    assert np.abs(wd).max() < 1e-13
+    # with a positive variable coefficient the Nyquist mode still loses energy
+    rng = np.random.default_rng(3)
+    for _ in range(5):
+        a = 1.0 + 0.5 * np.sin(2 * np.pi * np.arange(N) / N * rng.integers(1, 4) + rng.uniform(0, 6))
+        lu = stencil.narrow(np.pad(a, 4, mode="wrap"), np.pad(u, 4, mode="wrap"), 0, 1.0, M)
+        assert float(u @ lu) < 0.0
+
+
+def test_narrow6_exact_to_degree_7_and_default_parameter():
+    """6th-order stencil: exact for deg a + deg u <= 7 for any m36; the default
+    m36 = 281/3600 removes the a'''' u'''' truncation term (Sec. 2.2)."""
+    for m36 in (stencil.M36_SMC, Fr(220063, 1000000), Fr(0)):
+        M = stencil.narrow6_exact(m36)
+        for p in range(8):
+            for q in range(8 - p):
+                got = apply_exact(M, lambda x: Fr(x) ** p, lambda x: Fr(x) ** q, 1)
+                assert got == exact_second(p, q, 1)
+    x4 = lambda x: Fr(x) ** 4  # noqa: E731
+    assert apply_exact(stencil.narrow6_exact(stencil.M36_SMC), x4, x4, 0) == 0
+    assert apply_exact(stencil.narrow6_exact(Fr(220063, 1000000)), x4, x4, 0) != 0
+
+
+def test_first_derivative_exact_to_degree_8():
+    h = 0.5
+    x = h * np.arange(-8, 9)
+    for p in range(9):
+        f = x ** p
+        d = stencil.D(f, 0, h)
+        want = p * x[4:-4] ** (p - 1) if p else np.zeros(9)
+        assert np.allclose(d, want, rtol=1e-12, atol=1e-9)
+    assert not np.allclose(stencil.D(x ** 9, 0, h), 9 * x[4:-4] ** 8, rtol=1e-10)
+
+
+def test_narrow_float_matches_exact_rationals():
+    rng = np.random.default_rng(0)
+    M = stencil.narrow8_exact()
+    Mf = stencil.to_float(M)
+    a = rng.uniform(0.5, 2.0, 20)
+    u = rng.uniform(-1, 1, 20)
+    got = stencil.narrow(a, u, 0, 1.0, Mf)
+    for i in range(12):
+        want = apply_exact(M, lambda x: Fr(a[x + 4]), lambda x: Fr(u[x + 4]), i)
+        assert abs(got[i] - float(want)) < 1e-13
+
+
+@pytest.mark.parametrize("op", ["narrow", "D"])
+def test_order_eight_on_periodic_fields(op):
+    """Error ratio ~ 2^8 per halving of h for smooth periodic a and u."""
+    M = stencil.to_float(stencil.narrow8_exact())
+    errs = []
+    for N in (32, 64):
+        h = 2 * np.pi / N
+        x = h * np.arange(N)
+        a = 1.0 + 0.3 * np.sin(x + 0.4)
+        u = np.cos(2 * x) + 0.5 * np.sin(x)
+        if op == "narrow":
+            num = stencil.narrow(np.pad(a, 4, mode="wrap"), np.pad(u, 4, mode="wrap"), 0, h, M)
+            ux = -2 * np.sin(2 * x) + 0.5 * np.cos(x)
+            uxx = -4 * np.cos(2 * x) - 0.5 * np.sin(x)
+            ex = 0.3 * np.cos(x + 0.4) * ux + a * uxx
+        else:
+            num = stencil.D(np.pad(u, 4, mode="wrap"), 0, h)
+            ex = -2 * np.sin(2 * x) + 0.5 * np.cos(x)
+        errs.append(np.abs(num - ex).max())
+    rate = np.log2(errs[0] / errs[1])
+    assert 7.6 < rate < 8.5, rate
+
+
+def test_periodic_flux_form_telescopes():
+    rng = np.random.default_rng(1)
+    N = 40
+    a = rng.uniform(0.5, 2, N)
+    u = rng.normal(size=N)
+    M = stencil.to_float(stencil.narrow8_exact())
+    lu = stencil.narrow(np.pad(a, 4, mode="wrap"), np.pad(u, 4, mode="wrap"), 0, 1.0, M)
+    assert abs(lu.sum()) < 1e-12 * np.abs(lu).max() * N
+    du = stencil.D(np.pad(u, 4, mode="wrap"), 0, 1.0)
+    assert abs(du.sum()) < 1e-12 * np.abs(du).max() * N
