@@ -1,0 +1,341 @@
+"""Benchmark of the SMC hot path on GB300.
+
+A step is one time step of the configured integrator over the whole box
+array (every kernel of the path: ghost gather, primitives and transport,
+velocity gradients, the three stencil directions, correction-velocity and
+reaction terms, the SDC node updates or the multirate fine-node chains).
+
+Default workload ``c4``: 64 boxes of 16..64 cells per edge tiling a periodic
+domain, 21 species / 84 reactions, multirate SDC with 3 coarse
+(advection-diffusion) and 5 fine (reaction) Gauss-Lobatto nodes, 4 sweeps.
+
+value = cells x advection-diffusion RHS evaluations per step / time (Mcell-RHS/s),
+with K M1 = 8 such evaluations per multirate step after the first (the
+first value f(U_0) is recycled, Sec. 3.1); the K M2 reaction evaluations of
+the fine nodes are part of the step's time.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl smc|reference]
+                       [--workload c4] [--precision fp64]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+SM_COUNT = 152
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="smc", choices=["smc", "reference"])
+    ap.add_argument("--workload", default="c4")
+    ap.add_argument("--precision", default="fp64", choices=["fp64"])
+    ap.add_argument("--seed", type=int, default=1)
+    return ap.parse_args()
+
+
+def dist_setup(args):
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        dist.init_process_group(backend=backend)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(world, x, device):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def march_flops_per_cell(ns: int, mode: int = 0) -> float:
+    """FP64 flops one stencil-direction kernel (k_march) spends per cell,
+    counted from its source (an FMA is 2 flops): narrow-stencil face fluxes
+    508 + 143 ns, flux differences 4 + 2 ns, convective + mixed viscous D
+    225 + 21 ns, correction velocity 27 + 28 ns, accumulation 5 + ns."""
+    vc = 27 + 28 * ns if mode == 0 else 0
+    return 508 + 143 * ns + 4 + 2 * ns + 225 + 21 * ns + vc + 5 + ns
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
+
+
+def cpu_baseline(wl, budget_s: float = 15.0):
+    """The oracle's right-hand side on a bounded sample of the workload's boxes
+    (host cores, NumPy, single thread)."""
+    import numpy as np
+
+    from oracle import rhs as orhs
+    from oracle import thermo
+    from paper_1309_7327_gb300 import synth
+    g = wl.grid
+    prim = synth.boxes_to_global(g, wl.prim)
+    U = thermo.conserved(prim, wl.mech.nasa7, wl.mech.W)
+    # one box's worth of cells, evaluated as a ghosted patch of the global field
+    b = int(np.argmin([g.box_cells(i) for i in range(g.nboxes)]))
+    (x0, y0, z0), (x1, y1, z1) = g.lo[b], g.hi[b]
+    nz, ny, nx = U.shape[1:]
+    iz = np.arange(z0 - 4, z1 + 5) % nz
+    iy = np.arange(y0 - 4, y1 + 5) % ny
+    ix = np.arange(x0 - 4, x1 + 5) % nx
+    patch = U[:, iz][:, :, iy][:, :, :, ix]
+    cells = g.box_cells(b)
+    evals, t0 = 0, time.perf_counter()
+    while True:
+        orhs.rhs_ghosted(patch, wl.mech, g.dx)
+        evals += 1
+        el = time.perf_counter() - t0
+        if el > budget_s or evals >= 50:
+            break
+    return {"value": cells * evals / el / 1e6, "unit": "Mcell-RHS/s", "cores": 1,
+            "kind": "oracle",
+            "sample": f"{evals} full RHS evaluations of box {b} ({cells} cells) of workload "
+                      f"{wl.name} by the NumPy FP64 oracle, {el:.1f} s"}
+
+
+def run_reference(args):
+    """The oracle on the host cores (reference arm)."""
+    world, rank, local = int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")), 0
+    if rank != 0:
+        return
+    from paper_1309_7327_gb300 import synth
+    wl = synth.workload(args.workload, seed=args.seed)
+    for _ in range(args.warmup):
+        cpu_baseline(wl, budget_s=1.0)
+    vals = []
+    t0 = time.perf_counter()
+    last = None
+    for _ in range(args.steps):
+        last = cpu_baseline(wl, budget_s=5.0)
+        vals.append(last["value"])
+    el = time.perf_counter() - t0
+    value = statistics.mean(vals)
+    line = {"impl": "reference", "metric": "Mcell-RHS/s (21 species)", "value": value,
+            "unit": "Mcell-RHS/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1000 * el / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": args.workload},
+            "cpu_baseline": dict(last, value=value),
+            "e2e": {"value": value, "unit": "Mcell-RHS/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    world, rank, local = dist_setup(args)
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    __graft_entry__.build()
+    from paper_1309_7327_gb300 import smc, synth
+
+    wl = synth.workload(args.workload, seed=args.seed)
+    nodes, sweeps, rsub = wl.nodes, wl.sweeps, wl.reaction_substeps
+    M1 = nodes - 1
+    evals_per_step = sweeps * M1
+    ncells = wl.grid.ncells
+    nv = 5 + wl.mech.ns
+
+    h = smc.Smc(wl.grid, wl.mech)
+    stream = torch.cuda.Stream(device)
+    h.set_stream(stream)
+    prim = torch.from_numpy(wl.prim).to(device)
+    U = torch.empty_like(prim)
+    with torch.cuda.stream(stream):
+        h.prim_to_cons(prim, U)
+    h.synchronize()
+    del prim
+    U0 = U.clone()
+
+    # warm-up (also fills the recycled f(U_0))
+    for _ in range(args.warmup):
+        h.sdc_step(U, wl.dt, nodes, sweeps, rsub)
+    h.synchronize()
+    base = h.stats()
+    h.set_option("profile", 1)
+    sampler = ClockSampler(local)
+    barrier(world)
+    torch.cuda.synchronize(device)
+    sampler.start()
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    for _ in range(args.steps):
+        h.sdc_step(U, wl.dt, nodes, sweeps, rsub)
+    t_end.record(stream)
+    torch.cuda.synchronize(device)
+    clocks = sampler.stop()
+    barrier(world)
+    h.synchronize()
+    ms = t_start.elapsed_time(t_end)
+    ms = max_over_ranks(world, ms, device)
+    st = h.stats()
+    h.set_option("profile", 0)
+    launches = {k: st["launches"][k] - base["launches"][k] for k in st["launches"]}
+    kms = st["kernel_ms"]
+    ms_step = ms / args.steps
+    value = world * ncells * evals_per_step / (ms_step / 1e3) / 1e6
+
+    # dominant kernel: the stencil-direction kernel (FP64 pipe)
+    n_march = launches["march"]
+    march_ms = kms["march"] / max(n_march, 1)
+    flops_launch = march_flops_per_cell(wl.mech.ns) * ncells
+    sm_mhz = clocks.get("sm_mhz") or 2070.0
+    fp64_peak = SM_COUNT * 4 * sm_mhz * 1e6          # 2 DFMA / clk / SM (1.25 TFLOP/s at 2.07 GHz)
+    achieved = flops_launch / (march_ms / 1e3)
+    prof = os.path.join(ROOT, "profiles", "traffic.json")
+    traffic = None
+    if os.path.exists(prof):
+        try:
+            traffic = json.load(open(prof)).get(f"k_march:{args.workload}")
+        except ValueError:
+            traffic = None
+    roofline = {"bound": "alu", "kernel": "k_march (one stencil direction)",
+                "achieved": achieved / 1e12, "peak": fp64_peak / 1e12, "unit": "TFLOP/s",
+                "frac": achieved / fp64_peak, "traffic": traffic,
+                "peak_source": "FP64 pipe: 152 SMs x 2 FMA/clk x median SM clock under load"}
+    # HBM-bound stage: SDC / fine-node updates
+    peaks = measured_peaks()
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    # per fine-chain launch: U in + out, F1 (M1+3 arrays), F2 (fine group + 2) reads/writes
+    per = rsub - 1 if rsub >= 2 else 0
+    if per:
+        bytes_fine = ncells * 8 * (2 * nv + per * (M1 + 3) * nv + per * (rsub + 2) * wl.mech.ns)
+        fine_ms = kms["fine"] / max(launches["fine"], 1)
+        hbm = {"kernel": "k_fine_chain", "achieved_gbs": bytes_fine / (fine_ms / 1e3) / 1e9,
+               "peak_gbs": hbm_peak, "frac": bytes_fine / (fine_ms / 1e3) / 1e9 / hbm_peak,
+               "note": "algorithmic bytes; the chain also evaluates reactions in FP64"}
+    else:
+        hbm = None
+
+    # end to end: host buffers through the C ABI, copies inside the timed region
+    Uh = U0.cpu().numpy().copy()
+    h2 = smc.Smc(wl.grid, wl.mech)
+    h2.sdc_step(Uh, wl.dt, nodes, sweeps, rsub)
+    e2e_steps = max(1, min(args.steps, 3))
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        h2.sdc_step(Uh, wl.dt, nodes, sweeps, rsub)
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    e2e_s = max_over_ranks(world, e2e_s, device)
+    h2.close()
+    e2e = {"value": world * ncells * evals_per_step / e2e_s / 1e6, "unit": "Mcell-RHS/s",
+           "h2d_bytes_per_step": nv * ncells * 8, "d2h_bytes_per_step": nv * ncells * 8}
+
+    if rank == 0:
+        cpu = cpu_baseline(wl) if world == 1 else None
+        line = {
+            "metric": "Mcell-RHS/s (21 species)", "value": value, "unit": "Mcell-RHS/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": args.workload, "boxes": wl.grid.nboxes, "cells": ncells,
+                       "species": wl.mech.ns, "reactions": wl.mech.nr,
+                       "integrator": (f"MRSDC {nodes} coarse / {rsub} fine GL, {sweeps} sweeps"
+                                      if rsub >= 2 else f"SDC {nodes} GL, {sweeps} sweeps"),
+                       "rhs_evals_per_step": evals_per_step,
+                       "reaction_evals_per_step": sweeps * M1 * per if per else 0,
+                       "precision": args.precision,
+                       "l2": "inputs larger than L2 (state %.0f MB)" % (nv * ncells * 8 / 1e6),
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "roofline": roofline, "hbm": hbm, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": int(sum(launches.values())),
+            "kernel_ms_per_step": {k: kms[k] / args.steps for k in kms},
+            "clocks": clocks,
+        }
+        print(json.dumps(line))
+    h.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,213 @@
+/*
+ * smc.h -- C ABI of the GB300 (sm_103a) SMC hot path.
+ *
+ * The library evaluates the right-hand side of the multicomponent reacting
+ * compressible Navier-Stokes equations (Emmett, Zhang & Bell, arXiv
+ * 1309.7327, Sec. 2.1, eq. cns) on 3-D boxes of a structured grid with the
+ * paper's 8th-order spatial discretisation (Sec. 2.2), and advances it with
+ * spectral deferred corrections (Sec. 3.1, eq. expsdc) or mode-1 multirate
+ * SDC (Sec. 3.2, eq. mrupdate).  One GPU, one CUDA stream per handle.
+ *
+ * Units are CGS throughout (cm, g, s, K, erg); activation energies are in
+ * cal/mol.  All functions return an smc_status and never abort.
+ *
+ * Array layout ("box layout").  A field set of C components over the cells
+ * of all boxes is one contiguous array of doubles
+ *     a[c * ncells + offset(b) + (k * ny_b + j) * nx_b + i]
+ * component-major, boxes concatenated in grid order, each box [z][y][x]
+ * with x fastest, interior cells only (no ghost cells).  ncells is the sum
+ * of the boxes' cell counts.
+ *
+ * Conserved state U (NV = 5 + nspecies components, eq. cns):
+ *     rho, rho*u, rho*v, rho*w, rho*E, rho*Y_1 .. rho*Y_ns
+ * Primitive input of smc_prim_to_cons (NV components):
+ *     u, v, w, T, p, Y_1 .. Y_ns
+ *
+ * Pointers.  U, dUdt and prim may be device pointers (cudaMalloc'd, or a
+ * PyTorch CUDA tensor's data) or host pointers.  Device pointers are used in
+ * place and the call is asynchronous on the handle's stream.  Host pointers
+ * are staged through handle-owned device buffers and the call returns after
+ * the result is back in host memory.  The caller owns U, dUdt and prim; the
+ * handle owns everything else.
+ *
+ * Errors.  Argument errors are returned at once.  Conditions detected on the
+ * device (Newton non-convergence of the temperature, T <= 0 or rho <= 0,
+ * non-finite input) are recorded in a device status word and returned by the
+ * next synchronising call (smc_synchronize, or any call given host
+ * pointers).  smc_last_error gives a message for the last failure.
+ *
+ * Thread safety: a handle may be used by one host thread at a time.
+ */
+#ifndef SMC_H
+#define SMC_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct smc_handle smc_handle;
+
+typedef enum {
+  SMC_OK = 0,
+  SMC_ERR_ARG = 1,           /* invalid argument or unsupported configuration */
+  SMC_ERR_CUDA = 2,          /* a CUDA runtime call failed */
+  SMC_ERR_OOM = 3,           /* device allocation failed */
+  SMC_ERR_NONCONVERGED = 4,  /* temperature Newton iteration did not converge */
+  SMC_ERR_NONPHYSICAL = 5,   /* rho <= 0, T <= 0 or a non-finite value */
+  SMC_ERR_TIMEOUT = 6,       /* reserved: a bounded device wait gave up */
+  SMC_ERR_STATE = 7          /* call out of order (e.g. use after destroy) */
+} smc_status;
+
+/* Boxes of a BoxLib-style box array (Sec. 4).  Box b covers the global cells
+ * lo[3b..3b+2] .. hi[3b..3b+2] (inclusive, order x, y, z).  Boxes must not
+ * overlap, and every ghost cell (4 per side, Sec. 2.5) of every box must map,
+ * through the periodic wrap of the domain, onto a cell of some box. */
+typedef struct {
+  int nboxes;
+  const int *lo, *hi;        /* [3 * nboxes] */
+  int domain[3];             /* global cells in x, y, z */
+  double dx[3];              /* cell size in x, y, z (cm) */
+} smc_grid;
+
+/* A reversible mass-action mechanism and its mixture transport model.
+ * Thermodynamics: NASA 7-coefficient polynomials, one temperature range,
+ *   cp/R = a1 + a2 T + a3 T^2 + a4 T^3 + a5 T^4,
+ *   h/RT = a1 + a2 T/2 + a3 T^2/3 + a4 T^3/4 + a5 T^4/5 + a6/T,
+ *   s/R  = a1 ln T + a2 T + a3 T^2/2 + a4 T^3/3 + a5 T^4/4 + a7.
+ * Rates (rho*omega_k of eq. NS:rY): k_f = A T^b exp(-Ea / (R_c T)),
+ *   K_c = exp(-sum_k nu_k g_k/(R T)) (p_atm/(R_u T))^(sum_k nu_k),
+ *   k_r = k_f / K_c, q = k_f prod c^nu' - k_r prod c^nu''.
+ * Transport (the paper uses EGLIB; this library uses the model below):
+ *   eta = eta_ref (T/T_ref)^eta_exp, lambda = cp eta / Pr,
+ *   rho D_k = lambda / (cp Le_k), bulk viscosity xi = xi_ratio * eta.
+ * All arrays are host memory, copied by smc_create. */
+typedef struct {
+  int nspecies;              /* 1 .. 64 */
+  int nreactions;            /* 0 .. 1024 */
+  const double *W;           /* [ns] molecular weights, g/mol */
+  const double *nasa7;       /* [ns * 7] a1..a7 per species */
+  const int *nu_f;           /* [nr * ns] reactant coefficients (>= 0) */
+  const int *nu_r;           /* [nr * ns] product coefficients (>= 0) */
+  const double *A;           /* [nr] pre-exponential factors (mol, cm, s) */
+  const double *b;           /* [nr] temperature exponents */
+  const double *Ea;          /* [nr] activation energies, cal/mol */
+  const double *Le;          /* [ns] Lewis numbers */
+  double eta_ref, T_ref, eta_exp, Pr;
+} smc_mechanism;
+
+enum { SMC_BC_PERIODIC = 0, SMC_BC_OUTFLOW = 1 };
+/* Boundary kind of each domain face.  This version supports periodic faces
+ * only; any other value returns SMC_ERR_ARG. */
+typedef struct { int lo[3], hi[3]; } smc_bc;
+
+/* Options for smc_set_option (value given as a double). */
+enum {
+  SMC_OPT_PRECISION = 0,       /* 0: FP64 everywhere (default); 1: mixed */
+  SMC_OPT_M47 = 1,             /* free parameters of the 8th-order narrow */
+  SMC_OPT_M48 = 2,             /* stencil (Sec. 2.2); default 3557/44100, -2083/117600 */
+  SMC_OPT_DIFFUSION_MODE = 3,  /* 0: correction velocity (default, Sec. 2.4); 1: reference species */
+  SMC_OPT_REF_SPECIES = 4,     /* reference species index (default: last) */
+  SMC_OPT_XI_RATIO = 5,        /* bulk viscosity xi = value * eta (default 0) */
+  SMC_OPT_NEWTON_TOL = 6,      /* |dT| <= tol * T ends the iteration (default 1e-13) */
+  SMC_OPT_NEWTON_MAXIT = 7,    /* at most this many Newton steps (default 50) */
+  SMC_OPT_T_GUESS = 8,         /* Newton first guess in K (default 1000) */
+  SMC_OPT_REACTIONS = 9,       /* 1: include rho*omega_k (default); 0: omit */
+  SMC_OPT_SEGMENT = 10,        /* cells per thread along a stencil line (default 16) */
+  SMC_OPT_PROFILE = 11         /* 1: time every kernel launch with CUDA events (default 0) */
+};
+
+/* Kernel classes counted in smc_stats (launches always; times only while
+ * SMC_OPT_PROFILE is 1, summed over the handle's lifetime). */
+enum {
+  SMC_K_PRIM = 0,       /* primitives, transport, ghost-cell gather */
+  SMC_K_GRAD = 1,       /* velocity gradients for the mixed viscous terms */
+  SMC_K_MARCH = 2,      /* narrow stencils + convective D, one direction */
+  SMC_K_FINAL = 3,      /* correction-velocity terms and production rates */
+  SMC_K_UPDATE = 4,     /* SDC node update */
+  SMC_K_FINE = 5,       /* multirate fine-node reaction chain */
+  SMC_K_CHEM = 6,       /* reaction-only evaluation */
+  SMC_K_OTHER = 7,      /* primitive-to-conserved conversion */
+  SMC_NKERNELS = 8
+};
+
+typedef struct {
+  long long n_rhs;           /* advection-diffusion(-reaction) RHS evaluations */
+  long long n_react;         /* reaction-only evaluations (multirate fine nodes) */
+  long long n_steps;         /* smc_sdc_step calls completed */
+  unsigned int device_flags; /* last device status word read */
+  int nvars;                 /* NV = 5 + nspecies */
+  long long ncells;          /* interior cells over all boxes */
+  long long device_bytes;    /* device memory held by the handle */
+  long long launches[SMC_NKERNELS];   /* kernel launches per class */
+  double kernel_ms[SMC_NKERNELS];     /* summed device time per class (profiling on) */
+} smc_stats;
+
+/* Create a handle: validates the mechanism (element/mass balance sum_k
+ * nu_k W_k = 0 per reaction, cp > 0 on 200..3500 K) and the grid, uploads
+ * constants and builds the ghost-cell gather maps.  *out receives the
+ * handle.  The current CUDA device is used. */
+smc_status smc_create(const smc_grid *grid, const smc_mechanism *mech,
+                      const smc_bc *bc, smc_handle **out);
+
+/* Free the handle and everything it owns.  Accepts NULL. */
+smc_status smc_destroy(smc_handle *h);
+
+/* dUdt = full right-hand side of eq. cns at U (box layout, NV components):
+ * primitives and transport, -D of the convective fluxes (8th-order centred
+ * D), narrow-stencil (eqs. DaDu, H) viscous, conductive and diffusive terms,
+ * the correction-velocity or reference-species closure (Sec. 2.4), and the
+ * production rates.  Ghost cells are filled from U by periodic wrap. */
+smc_status smc_rhs(smc_handle *h, const double *U, double *dUdt);
+
+/* Advance U in place by one time step dt (s).
+ *   reaction_substeps <= 1: single-rate SDC, eq. expsdc, with `nodes`
+ *     Gauss-Lobatto nodes (3 or 5) and `sweeps` (>= 1) sweeps from the spread
+ *     initial guess; f(U_0) is recycled from the previous step when U is the
+ *     array the previous call left (call smc_invalidate after changing U).
+ *   reaction_substeps = Y >= 2: multirate SDC mode 1, eq. mrupdate: `nodes`
+ *     coarse Gauss-Lobatto nodes for advection-diffusion and Y Gauss-Lobatto
+ *     fine nodes in every coarse interval (type (b), Sec. 3.2) for the
+ *     reactions, Y <= 9. */
+smc_status smc_sdc_step(smc_handle *h, double *U, double dt, int nodes,
+                        int sweeps, int reaction_substeps);
+
+/* U from primitive fields (u, v, w, T, p, Y_k): rho from the ideal-gas law,
+ * rho E = rho (sum_k Y_k e_k(T) + |u|^2/2).  Same layout rules as U. */
+smc_status smc_prim_to_cons(smc_handle *h, const double *prim, double *U);
+
+/* Set the CUDA stream (a cudaStream_t) used by later calls; NULL = default. */
+smc_status smc_set_stream(smc_handle *h, void *stream);
+
+/* Set an SMC_OPT_* option; invalidates the recycled f(U_0). */
+smc_status smc_set_option(smc_handle *h, int key, double value);
+
+/* Counters and sizes. */
+smc_status smc_get_stats(smc_handle *h, smc_stats *out);
+
+/* Wait for the handle's stream, then return (and clear) any device-detected
+ * error. */
+smc_status smc_synchronize(smc_handle *h);
+
+/* Drop the cached f(U_0) of the last step. */
+smc_status smc_invalidate(smc_handle *h);
+
+/* Collocation data used by smc_sdc_step (host computation, no GPU needed).
+ * smc_collocation: the `nodes` Gauss-Lobatto nodes on [0, 1] (tau[nodes])
+ * and the node-to-node integration matrix S[(nodes-1) * nodes] of Sec. 3.1,
+ * s_mj = integral over [tau_m, tau_{m+1}] of the Lagrange polynomial L_j.
+ * smc_multirate_collocation: coarse nodes t1[coarse], fine nodes
+ * t2[M2 + 1] (M2 = (coarse-1)(fine-1), type (b) of Sec. 3.2), and the
+ * matrices S21[M2 * coarse] and S22[M2 * (M2 + 1)] of eq. mrupdate, per unit
+ * time step.  All arrays are caller-owned host memory. */
+smc_status smc_collocation(int nodes, double *tau, double *S);
+smc_status smc_multirate_collocation(int coarse, int fine, double *t1, double *t2,
+                                     double *S21, double *S22);
+
+/* Message describing the last error on this handle ("" if none).  The
+ * string is owned by the handle. */
+const char *smc_last_error(smc_handle *h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SMC_H */

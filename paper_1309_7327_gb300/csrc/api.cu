@@ -1,0 +1,877 @@
+// C ABI entry points and host orchestration (see include/smc.h).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "smc_internal.h"
+
+using namespace smc;
+
+struct smc_handle {
+  int ns = 0, nv = 0, nr = 0, nboxes = 0;
+  long long ncells = 0, nghost = 0;
+  std::vector<Box> boxes;
+  Mech hmech;
+  std::vector<Reaction> hrx;
+  Coef hcoef;
+  double dx[3] = {1, 1, 1};
+  double m47 = 3557.0 / 44100.0, m48 = -2083.0 / 117600.0;
+  Opts opt;
+  int precision = 0;
+  int segment = 16;
+  cudaStream_t stream = 0;
+  int device = 0;
+
+  Mech *d_mech = nullptr;
+  Reaction *d_rx = nullptr;
+  Box *d_boxes = nullptr;
+  int *d_gmap = nullptr;
+  long long *d_imap = nullptr;
+  LineItem *d_lines[3] = {nullptr, nullptr, nullptr};
+  long long nlines[3] = {0, 0, 0};
+  double *d_Q = nullptr, *d_G = nullptr, *d_divacc = nullptr;
+  unsigned *d_status = nullptr;
+
+  // integrator storage (allocated on first use)
+  std::vector<double *> fpool;          // NV-component arrays
+  std::vector<double *> rpool;          // ns-component arrays
+  double *d_U0 = nullptr;
+  double *d_stage[3] = {nullptr, nullptr, nullptr};
+
+  // recycled f(U_0) (Sec. 3.1): pool indices of the last step's end values
+  const double *cache_U = nullptr;
+  int cache_kind = 0;                   // 0 none, 1 single-rate, 2 multirate
+  int cache_f = -1, cache_r = -1;
+
+  long long n_rhs = 0, n_react = 0, n_steps = 0;
+  long long launches[SMC_NKERNELS] = {};
+  double kernel_ms[SMC_NKERNELS] = {};
+  int profile = 0;
+  std::vector<cudaEvent_t> ev_free;
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_pending;
+  unsigned last_flags = 0;
+  long long dev_bytes = 0;
+  std::string err;
+};
+
+namespace {
+
+smc_status fail(smc_handle *h, smc_status st, const std::string &msg) {
+  if (h) h->err = msg;
+  return st;
+}
+
+#define CUDA_TRY(h, call)                                                              \
+  do {                                                                                 \
+    cudaError_t e_ = (call);                                                           \
+    if (e_ != cudaSuccess)                                                             \
+      return fail((h), e_ == cudaErrorMemoryAllocation ? SMC_ERR_OOM : SMC_ERR_CUDA,    \
+                  std::string(#call) + ": " + cudaGetErrorString(e_));                 \
+  } while (0)
+
+template <class T>
+cudaError_t dalloc(smc_handle *h, T **p, size_t count) {
+  cudaError_t e = cudaMalloc((void **)p, count * sizeof(T) + 16);
+  if (e == cudaSuccess) h->dev_bytes += (long long)(count * sizeof(T));
+  return e;
+}
+
+// Bracket one kernel launch of class `kc`: counts it, and with profiling on
+// records a pair of events on the handle's stream.
+struct Timed {
+  smc_handle *h;
+  int kc;
+  cudaEvent_t a = nullptr, b = nullptr;
+  Timed(smc_handle *h_, int kc_) : h(h_), kc(kc_) {
+    h->launches[kc]++;
+    if (h->profile) {
+      a = take();
+      b = take();
+      cudaEventRecord(a, h->stream);
+    }
+  }
+  cudaEvent_t take() {
+    if (h->ev_free.empty()) {
+      cudaEvent_t e;
+      cudaEventCreate(&e);
+      return e;
+    }
+    cudaEvent_t e = h->ev_free.back();
+    h->ev_free.pop_back();
+    return e;
+  }
+  ~Timed() {
+    if (h->profile) {
+      cudaEventRecord(b, h->stream);
+      h->ev_pending.push_back({kc, {a, b}});
+    }
+  }
+};
+
+void collect_times(smc_handle *h) {
+  for (auto &p : h->ev_pending) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, p.second.first, p.second.second) == cudaSuccess)
+      h->kernel_ms[p.first] += ms;
+    h->ev_free.push_back(p.second.first);
+    h->ev_free.push_back(p.second.second);
+  }
+  h->ev_pending.clear();
+}
+
+DevState state(smc_handle *h) {
+  DevState s;
+  s.ns = h->ns;
+  s.nv = h->nv;
+  s.nq = nQ(h->ns);
+  s.nboxes = h->nboxes;
+  s.ncells = h->ncells;
+  s.nghost = h->nghost;
+  s.mech = h->d_mech;
+  s.rx = h->d_rx;
+  s.hcoef = &h->hcoef;
+  s.boxes = h->d_boxes;
+  s.gmap = h->d_gmap;
+  s.imap = h->d_imap;
+  for (int d = 0; d < 3; ++d) {
+    s.lines[d] = h->d_lines[d];
+    s.nlines[d] = h->nlines[d];
+  }
+  s.Q = h->d_Q;
+  s.G = h->d_G;
+  s.divacc = h->d_divacc;
+  s.status = h->d_status;
+  s.opt = h->opt;
+  return s;
+}
+
+void build_coef(smc_handle *h) {
+  // 8th-order narrow-stencil matrix M (Sec. 2.2), rows m = -3..4, cols n = -3..4
+  const double a = h->m47, b = h->m48;
+  double m[5][9] = {};
+  m[1][1] = 5.0 / 336 + b;
+  m[1][2] = -83.0 / 3600 - a / 5 - 14.0 * b / 5;
+  m[1][3] = 299.0 / 50400 + 2.0 * a / 5 + 13.0 * b / 5;
+  m[1][4] = 17.0 / 12600 - a / 5 - 4.0 * b / 5;
+  m[1][5] = 1.0 / 1120;
+  m[2][1] = -11.0 / 560 - 2 * b;
+  m[2][2] = -31.0 / 360 + a + 3 * b;
+  m[2][3] = 41.0 / 200 - 9.0 * a / 5 + 4.0 * b / 5;
+  m[2][4] = -5927.0 / 50400 + 4.0 * a / 5 - 9.0 * b / 5;
+  m[2][5] = 17.0 / 600 - a / 5 - 4.0 * b / 5;
+  m[2][6] = -503.0 / 50400 + a / 5 + 4.0 * b / 5;
+  m[3][1] = -1.0 / 280;
+  m[3][2] = 1097.0 / 5040 - 2 * a + 6 * b;
+  m[3][3] = -1349.0 / 10080 + 3 * a - 12 * b;
+  m[3][4] = -887.0 / 5040 - a + 6 * b;
+  m[3][5] = 3613.0 / 50400 + 4.0 * a / 5 - 9.0 * b / 5;
+  m[3][6] = 467.0 / 25200 - 3.0 * a / 5 + 18.0 * b / 5;
+  m[3][7] = 139.0 / 25200 - a / 5 - 9.0 * b / 5;
+  m[4][1] = 17.0 / 1680 + 2 * b;
+  m[4][2] = -319.0 / 2520 + 2 * a - 8 * b;
+  m[4][3] = -919.0 / 5040 - 2 * a + 6 * b;
+  m[4][4] = -445.0 / 2016;
+  m[4][5] = 583.0 / 720 - a + 6 * b;
+  m[4][6] = -65.0 / 224 - 7 * b;
+  m[4][7] = a;
+  m[4][8] = b;
+  double M[8][8] = {};
+  for (int r = 0; r < 4; ++r)
+    for (int c = 0; c < 8; ++c) {
+      M[r][c] = m[r + 1][c + 1];
+      M[7 - r][7 - c] = -m[r + 1][c + 1];
+    }
+  const double D8[4] = {4.0 / 5, -1.0 / 5, 4.0 / 105, -1.0 / 280};
+  for (int d = 0; d < 3; ++d) {
+    const double ih2 = 1.0 / (h->dx[d] * h->dx[d]);
+    for (int r = 0; r < 8; ++r)
+      for (int c = 0; c < 8; ++c) h->hcoef.M[d][r][c] = M[r][c] * ih2;
+    for (int k = 0; k < 4; ++k) h->hcoef.D[d][k] = D8[k] / h->dx[d];
+  }
+}
+
+smc_status build_lines(smc_handle *h) {
+  for (int d = 0; d < 3; ++d) {
+    if (h->d_lines[d]) cudaFree(h->d_lines[d]);
+    h->d_lines[d] = nullptr;
+    std::vector<LineItem> items;
+    for (int b = 0; b < h->nboxes; ++b) {
+      const Box &B = h->boxes[b];
+      const int n[3] = {B.nx, B.ny, B.nz};
+      const long long gs[3] = {1, B.gx, (long long)B.gx * B.gy};
+      const long long is[3] = {1, B.nx, (long long)B.nx * B.ny};
+      // transverse directions: inner = the one with the smaller stride
+      int e0 = (d == 0) ? 1 : 0;
+      int e1 = (d == 2) ? 1 : 2;
+      const int nd = n[d];
+      int nseg = (nd + h->segment - 1) / h->segment;
+      if (nseg < 1) nseg = 1;
+      for (int sgi = 0; sgi < nseg; ++sgi) {
+        const int s0 = (int)((long long)nd * sgi / nseg);
+        const int s1 = (int)((long long)nd * (sgi + 1) / nseg);
+        for (int t1 = 0; t1 < n[e1]; ++t1)
+          for (int t0 = 0; t0 < n[e0]; ++t0) {
+            LineItem L;
+            long long go = B.off_g, io = B.off_i;
+            int crd[3];
+            crd[d] = s0;
+            crd[e0] = t0;
+            crd[e1] = t1;
+            for (int k = 0; k < 3; ++k) {
+              go += (long long)(crd[k] + SMC_GHOST) * gs[k];
+              io += (long long)crd[k] * is[k];
+            }
+            L.g0 = go;
+            L.i0 = io;
+            L.sg = (int)gs[d];
+            L.si = (int)is[d];
+            L.len = s1 - s0;
+            L.pad = 0;
+            items.push_back(L);
+          }
+      }
+    }
+    h->nlines[d] = (long long)items.size();
+    CUDA_TRY(h, dalloc(h, &h->d_lines[d], items.size()));
+    CUDA_TRY(h, cudaMemcpy(h->d_lines[d], items.data(), items.size() * sizeof(LineItem),
+                           cudaMemcpyHostToDevice));
+  }
+  return SMC_OK;
+}
+
+bool is_device_ptr(const void *p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+smc_status check_flags(smc_handle *h) {
+  unsigned f = 0;
+  CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  collect_times(h);
+  CUDA_TRY(h, cudaMemcpy(&f, h->d_status, sizeof(unsigned), cudaMemcpyDeviceToHost));
+  CUDA_TRY(h, cudaMemset(h->d_status, 0, sizeof(unsigned)));
+  h->last_flags = f;
+  if (f & ST_NONCONV) return fail(h, SMC_ERR_NONCONVERGED, "temperature Newton iteration did not converge");
+  if (f & (ST_NONPHYS | ST_NONFINITE)) return fail(h, SMC_ERR_NONPHYSICAL, "non-physical or non-finite state (rho <= 0, T <= 0 or NaN)");
+  return SMC_OK;
+}
+
+smc_status ensure_stage(smc_handle *h, int i) {
+  if (!h->d_stage[i]) CUDA_TRY(h, dalloc(h, &h->d_stage[i], (size_t)h->nv * h->ncells));
+  return SMC_OK;
+}
+
+smc_status ensure_pools(smc_handle *h, int nf, int nr) {
+  while ((int)h->fpool.size() < nf) {
+    double *p = nullptr;
+    CUDA_TRY(h, dalloc(h, &p, (size_t)h->nv * h->ncells));
+    h->fpool.push_back(p);
+  }
+  while ((int)h->rpool.size() < nr) {
+    double *p = nullptr;
+    CUDA_TRY(h, dalloc(h, &p, (size_t)h->ns * h->ncells));
+    h->rpool.push_back(p);
+  }
+  if (!h->d_U0) CUDA_TRY(h, dalloc(h, &h->d_U0, (size_t)h->nv * h->ncells));
+  return SMC_OK;
+}
+
+// f(U) -> F on the device: transport (advection + diffusion) and/or reactions
+smc_status eval_rhs(smc_handle *h, const double *U, double *F, int transport, int chemistry) {
+  DevState s = state(h);
+  const int chem = chemistry && h->opt.reactions && h->nr > 0;
+  { Timed t(h, SMC_K_PRIM); launch_prim(s, U, h->stream); }
+  if (transport) {
+    { Timed t(h, SMC_K_GRAD); launch_grad(s, h->stream); }
+    for (int d = 0; d < 3; ++d) {
+      Timed t(h, SMC_K_MARCH);
+      launch_march(s, d, F, d == 0, h->stream);
+    }
+  }
+  { Timed t(h, SMC_K_FINAL); launch_final(s, F, transport, chem, h->stream); }
+  CUDA_TRY(h, cudaGetLastError());
+  return SMC_OK;
+}
+
+smc_status sdc_single_rate(smc_handle *h, double *U, const void *key, double dt, int nodes, int sweeps) {
+  const int M = nodes - 1;
+  std::vector<double> tau, S;
+  lobatto_nodes(nodes, tau);
+  node_to_node_matrix(tau, S);
+  // pool: index 0..2M (one shared start value + two sets of M node values)
+  smc_status st = ensure_pools(h, 2 * M + 1, 0);
+  if (st) return st;
+  const long long n = (long long)h->nv * h->ncells;
+  CUDA_TRY(h, cudaMemcpyAsync(h->d_U0, U, n * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+  int f0;
+  if (h->cache_kind == 1 && h->cache_U == key && h->cache_f >= 0) {
+    f0 = h->cache_f;
+  } else {
+    f0 = 0;
+    st = eval_rhs(h, h->d_U0, h->fpool[f0], 1, 1);
+    if (st) return st;
+    h->n_rhs++;
+  }
+  std::vector<int> others;
+  for (int i = 0; i < 2 * M + 1; ++i)
+    if (i != f0) others.push_back(i);
+  std::vector<int> fold(M + 1, f0), fnew(M + 1, f0);
+  int set = 0;
+  for (int k = 0; k < sweeps; ++k) {
+    fnew[0] = f0;
+    for (int m = 1; m <= M; ++m) fnew[m] = others[set * M + (m - 1)];
+    for (int m = 0; m < M; ++m) {
+      if (m > 0) {
+        st = eval_rhs(h, U, h->fpool[fnew[m]], 1, 1);
+        if (st) return st;
+        h->n_rhs++;
+      }
+      // eq. expsdc: U_{m+1} = U_m + dt_m (F^{k+1}_m - F^k_m) + dt (S F^k)_m
+      const double dtm = dt * (tau[m + 1] - tau[m]);
+      Combo cb;
+      cb.nsrc = 0;
+      cb.c[cb.nsrc] = dtm;
+      cb.src[cb.nsrc++] = h->fpool[fnew[m]];
+      cb.c[cb.nsrc] = -dtm;
+      cb.src[cb.nsrc++] = h->fpool[fold[m]];
+      for (int j = 0; j <= M; ++j) {
+        cb.c[cb.nsrc] = dt * S[m * (M + 1) + j];
+        cb.src[cb.nsrc++] = h->fpool[fold[j]];
+      }
+      Timed t(h, SMC_K_UPDATE);
+      launch_combo(m == 0 ? h->d_U0 : U, U, cb, n, h->stream);
+    }
+    st = eval_rhs(h, U, h->fpool[fnew[M]], 1, 1);
+    if (st) return st;
+    h->n_rhs++;
+    fold = fnew;
+    set ^= 1;
+  }
+  CUDA_TRY(h, cudaGetLastError());
+  h->cache_kind = 1;
+  h->cache_U = (const double *)key;
+  h->cache_f = fold[M];
+  h->cache_r = -1;
+  return SMC_OK;
+}
+
+smc_status sdc_multirate(smc_handle *h, double *U, const void *key, double dt, int coarse, int sweeps,
+                         int fine) {
+  const int M1 = coarse - 1, per = fine - 1, M2 = M1 * per;
+  if (M1 > 4 || per > 8 || M2 > 32) return fail(h, SMC_ERR_ARG, "too many multirate nodes");
+  std::vector<double> t1, t2, S21, S22;
+  multirate_matrices(coarse, fine, t1, t2, S21, S22);
+  smc_status st = ensure_pools(h, 2 * M1 + 1, 2 * M2 + 1);
+  if (st) return st;
+  const long long n = (long long)h->nv * h->ncells;
+  CUDA_TRY(h, cudaMemcpyAsync(h->d_U0, U, n * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+  int f0, r0;
+  if (h->cache_kind == 2 && h->cache_U == key && h->cache_f >= 0 && h->cache_r >= 0) {
+    f0 = h->cache_f;
+    r0 = h->cache_r;
+  } else {
+    f0 = 0;
+    r0 = 0;
+    st = eval_rhs(h, h->d_U0, h->fpool[f0], 1, 0);
+    if (st) return st;
+    { Timed t(h, SMC_K_CHEM); launch_chem_only(state(h), h->d_U0, h->rpool[r0], h->stream); }
+    h->n_rhs++;
+    h->n_react++;
+  }
+  std::vector<int> fo, ro;
+  for (int i = 0; i < 2 * M1 + 1; ++i)
+    if (i != f0) fo.push_back(i);
+  for (int i = 0; i < 2 * M2 + 1; ++i)
+    if (i != r0) ro.push_back(i);
+  std::vector<int> f1old(M1 + 1, f0), f1new(M1 + 1, f0), f2old(M2 + 1, r0), f2new(M2 + 1, r0);
+  int set = 0;
+  DevState s = state(h);
+  for (int k = 0; k < sweeps; ++k) {
+    f1new[0] = f0;
+    f2new[0] = r0;
+    for (int p = 1; p <= M1; ++p) f1new[p] = fo[set * M1 + p - 1];
+    for (int q = 1; q <= M2; ++q) f2new[q] = ro[set * M2 + q - 1];
+    for (int p = 0; p < M1; ++p) {
+      if (p > 0) {
+        st = eval_rhs(h, U, h->fpool[f1new[p]], 1, 0);
+        if (st) return st;
+        h->n_rhs++;
+      }
+      FineChain fc;
+      memset(&fc, 0, sizeof(fc));
+      fc.q0 = p * per;
+      fc.nsub = per;
+      fc.p = p;
+      fc.M1 = M1;
+      for (int sidx = 0; sidx < per; ++sidx) {
+        const int q = fc.q0 + sidx;
+        fc.dtq[sidx] = dt * (t2[q + 1] - t2[q]);
+        for (int j = 0; j <= M1; ++j) fc.s21[sidx][j] = dt * S21[q * (M1 + 1) + j];
+        for (int t = 0; t <= per; ++t) fc.s22[sidx][t] = dt * S22[q * (M2 + 1) + fc.q0 + t];
+      }
+      fc.F1new_p = h->fpool[f1new[p]];
+      fc.F1old_p = h->fpool[f1old[p]];
+      for (int j = 0; j <= M1; ++j) fc.F1old[j] = h->fpool[f1old[j]];
+      for (int t = 0; t <= per; ++t) {
+        fc.F2old[t] = h->rpool[f2old[fc.q0 + t]];
+        fc.F2new[t] = h->rpool[f2new[fc.q0 + t]];
+      }
+      fc.eval_first = fc.q0 > 0;
+      fc.eval_last = (p == M1 - 1);
+      { Timed t(h, SMC_K_FINE); launch_fine_chain(s, p == 0 ? h->d_U0 : U, U, fc, h->stream); }
+      h->n_react += per - (fc.eval_first ? 0 : 1) + (fc.eval_last ? 1 : 0);
+    }
+    st = eval_rhs(h, U, h->fpool[f1new[M1]], 1, 0);
+    if (st) return st;
+    h->n_rhs++;
+    f1old = f1new;
+    f2old = f2new;
+    set ^= 1;
+  }
+  CUDA_TRY(h, cudaGetLastError());
+  h->cache_kind = 2;
+  h->cache_U = (const double *)key;
+  h->cache_f = f1old[M1];
+  h->cache_r = f2old[M2];
+  return SMC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+smc_status smc_create(const smc_grid *grid, const smc_mechanism *mech, const smc_bc *bc,
+                      smc_handle **out) {
+  if (!out) return SMC_ERR_ARG;
+  *out = nullptr;
+  if (!grid || !mech) return SMC_ERR_ARG;
+  smc_handle *h = new smc_handle();
+  auto bail = [&](smc_status st) {
+    // keep the handle so the caller can read the message, but free device memory
+    *out = h;
+    return st;
+  };
+  if (bc) {
+    for (int d = 0; d < 3; ++d)
+      if (bc->lo[d] != SMC_BC_PERIODIC || bc->hi[d] != SMC_BC_PERIODIC)
+        return bail(fail(h, SMC_ERR_ARG, "only periodic boundaries are supported"));
+  }
+  // ---- mechanism
+  const int ns = mech->nspecies, nr = mech->nreactions;
+  if (ns < 1 || ns > SMC_MAX_NS) return bail(fail(h, SMC_ERR_ARG, "nspecies must be 1..64"));
+  if (nr < 0 || nr > 1024) return bail(fail(h, SMC_ERR_ARG, "nreactions must be 0..1024"));
+  if (!mech->W || !mech->nasa7 || !mech->Le || (nr > 0 && (!mech->nu_f || !mech->nu_r || !mech->A ||
+                                                           !mech->b || !mech->Ea)))
+    return bail(fail(h, SMC_ERR_ARG, "null mechanism array"));
+  h->ns = ns;
+  h->nv = 5 + ns;
+  h->nr = nr;
+  Mech &M = h->hmech;
+  memset(&M, 0, sizeof(M));
+  M.ns = ns;
+  M.nr = nr;
+  for (int k = 0; k < ns; ++k) {
+    const double W = mech->W[k];
+    if (!(W > 0) || !(mech->Le[k] > 0)) return bail(fail(h, SMC_ERR_ARG, "W and Le must be positive"));
+    const double *a = mech->nasa7 + 7 * k;
+    M.W[k] = W;
+    M.invW[k] = 1.0 / W;
+    M.Ru_W[k] = kRu / W;
+    M.invLe[k] = 1.0 / mech->Le[k];
+    for (int i = 0; i < 5; ++i) M.cp[k][i] = a[i];
+    M.hT[k][0] = a[5];
+    M.hT[k][1] = a[0];
+    M.hT[k][2] = a[1] / 2;
+    M.hT[k][3] = a[2] / 3;
+    M.hT[k][4] = a[3] / 4;
+    M.hT[k][5] = a[4] / 5;
+    M.sR[k][0] = a[0];
+    M.sR[k][1] = a[6];
+    M.sR[k][2] = a[1];
+    M.sR[k][3] = a[2] / 2;
+    M.sR[k][4] = a[3] / 3;
+    M.sR[k][5] = a[4] / 4;
+    for (int i = 0; i <= 100; ++i) {
+      const double T = 200.0 + 33.0 * i;
+      const double cp = a[0] + T * (a[1] + T * (a[2] + T * (a[3] + T * a[4])));
+      if (!(cp > 0)) return bail(fail(h, SMC_ERR_ARG, "cp must be positive on 200..3500 K"));
+    }
+  }
+  if (!(mech->eta_ref > 0) || !(mech->T_ref > 0) || !(mech->Pr > 0))
+    return bail(fail(h, SMC_ERR_ARG, "transport parameters must be positive"));
+  M.eta_ref = mech->eta_ref;
+  M.inv_T_ref = 1.0 / mech->T_ref;
+  M.eta_exp = mech->eta_exp;
+  M.inv_Pr = 1.0 / mech->Pr;
+  h->hrx.resize(nr);
+  for (int r = 0; r < nr; ++r) {
+    Reaction &R = h->hrx[r];
+    memset(&R, 0, sizeof(R));
+    if (!(mech->A[r] > 0)) return bail(fail(h, SMC_ERR_ARG, "A must be positive"));
+    R.lnA = log(mech->A[r]);
+    R.b = mech->b[r];
+    R.Ea_R = mech->Ea[r] / kRc;
+    double dnu = 0, mass = 0, scale = 0;
+    for (int k = 0; k < ns; ++k) {
+      const int f = mech->nu_f[r * ns + k], p = mech->nu_r[r * ns + k];
+      if (f < 0 || p < 0) return bail(fail(h, SMC_ERR_ARG, "negative stoichiometric coefficient"));
+      if (f > 0) {
+        if (R.nf == SMC_MAX_SIDE) return bail(fail(h, SMC_ERR_ARG, "more than 4 reactant species"));
+        R.fk[R.nf] = k;
+        R.fc[R.nf++] = f;
+      }
+      if (p > 0) {
+        if (R.nr_ == SMC_MAX_SIDE) return bail(fail(h, SMC_ERR_ARG, "more than 4 product species"));
+        R.rk[R.nr_] = k;
+        R.rc[R.nr_++] = p;
+      }
+      dnu += p - f;
+      mass += (p - f) * mech->W[k];
+      scale += (p + f) * mech->W[k];
+    }
+    if (R.nf == 0 || R.nr_ == 0) return bail(fail(h, SMC_ERR_ARG, "empty reaction side"));
+    if (fabs(mass) > 1e-9 * scale) return bail(fail(h, SMC_ERR_ARG, "reaction does not conserve mass"));
+    R.dnu = dnu;
+  }
+  // ---- grid
+  if (grid->nboxes < 1 || !grid->lo || !grid->hi) return bail(fail(h, SMC_ERR_ARG, "no boxes"));
+  for (int d = 0; d < 3; ++d) {
+    if (grid->domain[d] < 1) return bail(fail(h, SMC_ERR_ARG, "empty domain"));
+    if (!(grid->dx[d] > 0)) return bail(fail(h, SMC_ERR_ARG, "dx must be positive"));
+    h->dx[d] = grid->dx[d];
+  }
+  const long long D0 = grid->domain[0], D1 = grid->domain[1], D2 = grid->domain[2];
+  std::vector<int> owner((size_t)(D0 * D1 * D2), -1);
+  h->nboxes = grid->nboxes;
+  h->boxes.resize(h->nboxes);
+  long long offg = 0, offi = 0;
+  for (int b = 0; b < h->nboxes; ++b) {
+    Box &B = h->boxes[b];
+    int n[3];
+    for (int d = 0; d < 3; ++d) {
+      const int lo = grid->lo[3 * b + d], hi = grid->hi[3 * b + d];
+      if (lo < 0 || hi < lo || hi >= grid->domain[d])
+        return bail(fail(h, SMC_ERR_ARG, "box outside the domain"));
+      n[d] = hi - lo + 1;
+    }
+    B.nx = n[0];
+    B.ny = n[1];
+    B.nz = n[2];
+    B.gx = n[0] + 2 * SMC_GHOST;
+    B.gy = n[1] + 2 * SMC_GHOST;
+    B.gz = n[2] + 2 * SMC_GHOST;
+    B.off_g = offg;
+    B.off_i = offi;
+    offg += (long long)B.gx * B.gy * B.gz;
+    offi += (long long)B.nx * B.ny * B.nz;
+    for (int k = 0; k < n[2]; ++k)
+      for (int j = 0; j < n[1]; ++j)
+        for (int i = 0; i < n[0]; ++i) {
+          const long long gidx = ((long long)(grid->lo[3 * b + 2] + k) * D1 + grid->lo[3 * b + 1] + j) * D0 +
+                                 grid->lo[3 * b] + i;
+          if (owner[gidx] >= 0) return bail(fail(h, SMC_ERR_ARG, "boxes overlap"));
+          owner[gidx] = b;
+        }
+  }
+  h->ncells = offi;
+  h->nghost = offg;
+  if (h->nghost >= (1LL << 31) || h->ncells * (long long)h->nv >= (1LL << 62))
+    return bail(fail(h, SMC_ERR_ARG, "grid too large"));
+  std::vector<int> gmap((size_t)h->nghost);
+  std::vector<long long> imap((size_t)h->ncells);
+  for (int b = 0; b < h->nboxes; ++b) {
+    const Box &B = h->boxes[b];
+    for (int k = -SMC_GHOST; k < B.nz + SMC_GHOST; ++k)
+      for (int j = -SMC_GHOST; j < B.ny + SMC_GHOST; ++j)
+        for (int i = -SMC_GHOST; i < B.nx + SMC_GHOST; ++i) {
+          const long long x = ((grid->lo[3 * b] + i) % D0 + D0) % D0;
+          const long long y = ((grid->lo[3 * b + 1] + j) % D1 + D1) % D1;
+          const long long z = ((grid->lo[3 * b + 2] + k) % D2 + D2) % D2;
+          const int ob = owner[(z * D1 + y) * D0 + x];
+          if (ob < 0) return bail(fail(h, SMC_ERR_ARG, "a ghost cell maps onto no box"));
+          const Box &O = h->boxes[ob];
+          const long long li = ((z - grid->lo[3 * ob + 2]) * O.ny + (y - grid->lo[3 * ob + 1])) * O.nx +
+                               (x - grid->lo[3 * ob]);
+          const long long g = B.off_g + ((long long)(k + SMC_GHOST) * B.gy + (j + SMC_GHOST)) * B.gx +
+                              (i + SMC_GHOST);
+          gmap[g] = (int)(O.off_i + li);
+          if (i >= 0 && i < B.nx && j >= 0 && j < B.ny && k >= 0 && k < B.nz)
+            imap[B.off_i + ((long long)k * B.ny + j) * B.nx + i] = g;
+        }
+  }
+  if (h->ncells >= (1LL << 31)) return bail(fail(h, SMC_ERR_ARG, "grid too large"));
+  // ---- options
+  h->opt.mode = 0;
+  h->opt.ref = ns - 1;
+  h->opt.reactions = 1;
+  h->opt.maxit = 50;
+  h->opt.tol = 1e-13;
+  h->opt.T0 = 1000.0;
+  h->opt.xi_ratio = 0.0;
+  build_coef(h);
+  cudaGetDevice(&h->device);
+  // ---- device memory
+#define TRY_ALLOC(call)                                   \
+  do {                                                    \
+    smc_status st_ = SMC_OK;                              \
+    cudaError_t e_ = (call);                              \
+    if (e_ != cudaSuccess) {                              \
+      st_ = fail(h, e_ == cudaErrorMemoryAllocation ? SMC_ERR_OOM : SMC_ERR_CUDA, \
+                 std::string("allocation: ") + cudaGetErrorString(e_));           \
+      return bail(st_);                                   \
+    }                                                     \
+  } while (0)
+  TRY_ALLOC(dalloc(h, &h->d_mech, 1));
+  TRY_ALLOC(cudaMemcpy(h->d_mech, &h->hmech, sizeof(Mech), cudaMemcpyHostToDevice));
+  TRY_ALLOC(dalloc(h, &h->d_rx, std::max(nr, 1)));
+  if (nr) TRY_ALLOC(cudaMemcpy(h->d_rx, h->hrx.data(), nr * sizeof(Reaction), cudaMemcpyHostToDevice));
+  TRY_ALLOC(dalloc(h, &h->d_boxes, h->nboxes));
+  TRY_ALLOC(cudaMemcpy(h->d_boxes, h->boxes.data(), h->nboxes * sizeof(Box), cudaMemcpyHostToDevice));
+  TRY_ALLOC(dalloc(h, &h->d_gmap, (size_t)h->nghost));
+  TRY_ALLOC(cudaMemcpy(h->d_gmap, gmap.data(), gmap.size() * sizeof(int), cudaMemcpyHostToDevice));
+  TRY_ALLOC(dalloc(h, &h->d_imap, (size_t)h->ncells));
+  TRY_ALLOC(cudaMemcpy(h->d_imap, imap.data(), imap.size() * sizeof(long long), cudaMemcpyHostToDevice));
+  TRY_ALLOC(dalloc(h, &h->d_Q, (size_t)nQ(ns) * h->nghost));
+  TRY_ALLOC(dalloc(h, &h->d_G, (size_t)9 * h->nghost));
+  TRY_ALLOC(cudaMemset(h->d_G, 0, (size_t)9 * h->nghost * sizeof(double)));
+  TRY_ALLOC(dalloc(h, &h->d_divacc, (size_t)h->ncells));
+  TRY_ALLOC(dalloc(h, &h->d_status, 1));
+  TRY_ALLOC(cudaMemset(h->d_status, 0, sizeof(unsigned)));
+  smc_status st = build_lines(h);
+  if (st) return bail(st);
+  *out = h;
+  return SMC_OK;
+}
+
+smc_status smc_destroy(smc_handle *h) {
+  if (!h) return SMC_OK;
+  cudaStreamSynchronize(h->stream);
+  cudaFree(h->d_mech);
+  cudaFree(h->d_rx);
+  cudaFree(h->d_boxes);
+  cudaFree(h->d_gmap);
+  cudaFree(h->d_imap);
+  for (int d = 0; d < 3; ++d) cudaFree(h->d_lines[d]);
+  cudaFree(h->d_Q);
+  cudaFree(h->d_G);
+  cudaFree(h->d_divacc);
+  cudaFree(h->d_status);
+  for (double *p : h->fpool) cudaFree(p);
+  for (double *p : h->rpool) cudaFree(p);
+  cudaFree(h->d_U0);
+  for (int i = 0; i < 3; ++i) cudaFree(h->d_stage[i]);
+  for (auto &p : h->ev_pending) {
+    h->ev_free.push_back(p.second.first);
+    h->ev_free.push_back(p.second.second);
+  }
+  for (cudaEvent_t e : h->ev_free) cudaEventDestroy(e);
+  delete h;
+  return SMC_OK;
+}
+
+smc_status smc_rhs(smc_handle *h, const double *U, double *dUdt) {
+  if (!h || !h->d_Q) return SMC_ERR_STATE;
+  if (!U || !dUdt) return fail(h, SMC_ERR_ARG, "null pointer");
+  const bool du = is_device_ptr(U), df = is_device_ptr(dUdt);
+  const size_t bytes = (size_t)h->nv * h->ncells * sizeof(double);
+  const double *Ud = U;
+  double *Fd = dUdt;
+  smc_status st;
+  if (!du) {
+    if ((st = ensure_stage(h, 0))) return st;
+    CUDA_TRY(h, cudaMemcpyAsync(h->d_stage[0], U, bytes, cudaMemcpyHostToDevice, h->stream));
+    Ud = h->d_stage[0];
+  }
+  if (!df) {
+    if ((st = ensure_stage(h, 1))) return st;
+    Fd = h->d_stage[1];
+  }
+  st = eval_rhs(h, Ud, Fd, 1, 1);
+  if (st) return st;
+  h->n_rhs++;
+  if (!df) CUDA_TRY(h, cudaMemcpyAsync(dUdt, Fd, bytes, cudaMemcpyDeviceToHost, h->stream));
+  if (!du || !df) return check_flags(h);
+  return SMC_OK;
+}
+
+smc_status smc_sdc_step(smc_handle *h, double *U, double dt, int nodes, int sweeps,
+                        int reaction_substeps) {
+  if (!h || !h->d_Q) return SMC_ERR_STATE;
+  if (!U) return fail(h, SMC_ERR_ARG, "null pointer");
+  if (!(dt > 0) || !std::isfinite(dt)) return fail(h, SMC_ERR_ARG, "dt must be positive");
+  if (nodes != 3 && nodes != 5) return fail(h, SMC_ERR_ARG, "nodes must be 3 or 5");
+  if (sweeps < 1 || sweeps > 64) return fail(h, SMC_ERR_ARG, "sweeps must be 1..64");
+  if (reaction_substeps < 0 || reaction_substeps > 9)
+    return fail(h, SMC_ERR_ARG, "reaction_substeps must be 0..9");
+  const bool dev = is_device_ptr(U);
+  const size_t bytes = (size_t)h->nv * h->ncells * sizeof(double);
+  double *Ud = U;
+  smc_status st;
+  if (!dev) {
+    if ((st = ensure_stage(h, 2))) return st;
+    CUDA_TRY(h, cudaMemcpyAsync(h->d_stage[2], U, bytes, cudaMemcpyHostToDevice, h->stream));
+    Ud = h->d_stage[2];
+  }
+  // the recycled f(U_0) is keyed by the caller's pointer (host or device)
+  if (reaction_substeps <= 1)
+    st = sdc_single_rate(h, Ud, U, dt, nodes, sweeps);
+  else
+    st = sdc_multirate(h, Ud, U, dt, nodes, sweeps, reaction_substeps);
+  if (st) return st;
+  h->n_steps++;
+  if (!dev) {
+    CUDA_TRY(h, cudaMemcpyAsync(U, Ud, bytes, cudaMemcpyDeviceToHost, h->stream));
+    return check_flags(h);
+  }
+  return SMC_OK;
+}
+
+smc_status smc_prim_to_cons(smc_handle *h, const double *prim, double *U) {
+  if (!h || !h->d_Q) return SMC_ERR_STATE;
+  if (!prim || !U) return fail(h, SMC_ERR_ARG, "null pointer");
+  const bool dp = is_device_ptr(prim), du = is_device_ptr(U);
+  const size_t bytes = (size_t)h->nv * h->ncells * sizeof(double);
+  const double *Pd = prim;
+  double *Ud = U;
+  smc_status st;
+  if (!dp) {
+    if ((st = ensure_stage(h, 0))) return st;
+    CUDA_TRY(h, cudaMemcpyAsync(h->d_stage[0], prim, bytes, cudaMemcpyHostToDevice, h->stream));
+    Pd = h->d_stage[0];
+  }
+  if (!du) {
+    if ((st = ensure_stage(h, 1))) return st;
+    Ud = h->d_stage[1];
+  }
+  { Timed t(h, SMC_K_OTHER); launch_prim_to_cons(state(h), Pd, Ud, h->stream); }
+  CUDA_TRY(h, cudaGetLastError());
+  if (!du) CUDA_TRY(h, cudaMemcpyAsync(U, Ud, bytes, cudaMemcpyDeviceToHost, h->stream));
+  if (!dp || !du) CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  return SMC_OK;
+}
+
+smc_status smc_set_stream(smc_handle *h, void *stream) {
+  if (!h) return SMC_ERR_STATE;
+  h->stream = (cudaStream_t)stream;
+  return SMC_OK;
+}
+
+smc_status smc_set_option(smc_handle *h, int key, double v) {
+  if (!h) return SMC_ERR_STATE;
+  h->cache_kind = 0;
+  switch (key) {
+    case SMC_OPT_PRECISION:
+      if (v != 0.0 && v != 1.0) return fail(h, SMC_ERR_ARG, "precision must be 0 or 1");
+      if (v == 1.0) return fail(h, SMC_ERR_ARG, "mixed precision is not available in this build");
+      h->precision = (int)v;
+      return SMC_OK;
+    case SMC_OPT_M47: h->m47 = v; build_coef(h); return SMC_OK;
+    case SMC_OPT_M48: h->m48 = v; build_coef(h); return SMC_OK;
+    case SMC_OPT_DIFFUSION_MODE:
+      if (v != 0.0 && v != 1.0) return fail(h, SMC_ERR_ARG, "diffusion mode must be 0 or 1");
+      h->opt.mode = (int)v;
+      return SMC_OK;
+    case SMC_OPT_REF_SPECIES:
+      if (v < 0 || v >= h->ns || v != floor(v)) return fail(h, SMC_ERR_ARG, "bad reference species");
+      h->opt.ref = (int)v;
+      return SMC_OK;
+    case SMC_OPT_XI_RATIO: h->opt.xi_ratio = v; return SMC_OK;
+    case SMC_OPT_NEWTON_TOL:
+      if (!(v > 0)) return fail(h, SMC_ERR_ARG, "tolerance must be positive");
+      h->opt.tol = v;
+      return SMC_OK;
+    case SMC_OPT_NEWTON_MAXIT:
+      if (v < 1 || v > 1000) return fail(h, SMC_ERR_ARG, "maxit must be 1..1000");
+      h->opt.maxit = (int)v;
+      return SMC_OK;
+    case SMC_OPT_T_GUESS:
+      if (!(v > 0)) return fail(h, SMC_ERR_ARG, "guess must be positive");
+      h->opt.T0 = v;
+      return SMC_OK;
+    case SMC_OPT_REACTIONS: h->opt.reactions = v != 0.0; return SMC_OK;
+    case SMC_OPT_PROFILE:
+      cudaStreamSynchronize(h->stream);
+      collect_times(h);
+      h->profile = v != 0.0;
+      return SMC_OK;
+    case SMC_OPT_SEGMENT: {
+      if (v < 1 || v > 4096) return fail(h, SMC_ERR_ARG, "segment must be 1..4096");
+      h->segment = (int)v;
+      cudaStreamSynchronize(h->stream);
+      return build_lines(h);
+    }
+    default:
+      return fail(h, SMC_ERR_ARG, "unknown option");
+  }
+}
+
+smc_status smc_get_stats(smc_handle *h, smc_stats *o) {
+  if (!h || !o) return SMC_ERR_ARG;
+  o->n_rhs = h->n_rhs;
+  o->n_react = h->n_react;
+  o->n_steps = h->n_steps;
+  o->device_flags = h->last_flags;
+  o->nvars = h->nv;
+  o->ncells = h->ncells;
+  o->device_bytes = h->dev_bytes;
+  if (h->profile) {
+    cudaStreamSynchronize(h->stream);
+    collect_times(h);
+  }
+  for (int k = 0; k < SMC_NKERNELS; ++k) {
+    o->launches[k] = h->launches[k];
+    o->kernel_ms[k] = h->kernel_ms[k];
+  }
+  return SMC_OK;
+}
+
+smc_status smc_synchronize(smc_handle *h) {
+  if (!h) return SMC_ERR_STATE;
+  return check_flags(h);
+}
+
+smc_status smc_invalidate(smc_handle *h) {
+  if (!h) return SMC_ERR_STATE;
+  h->cache_kind = 0;
+  h->cache_U = nullptr;
+  return SMC_OK;
+}
+
+smc_status smc_collocation(int nodes, double *tau, double *S) {
+  if (nodes < 2 || nodes > 16 || !tau || !S) return SMC_ERR_ARG;
+  std::vector<double> t, s;
+  lobatto_nodes(nodes, t);
+  node_to_node_matrix(t, s);
+  std::copy(t.begin(), t.end(), tau);
+  std::copy(s.begin(), s.end(), S);
+  return SMC_OK;
+}
+
+smc_status smc_multirate_collocation(int coarse, int fine, double *t1, double *t2, double *S21,
+                                     double *S22) {
+  if (coarse < 2 || coarse > 9 || fine < 2 || fine > 9 || !t1 || !t2 || !S21 || !S22)
+    return SMC_ERR_ARG;
+  std::vector<double> a, b, c, d;
+  multirate_matrices(coarse, fine, a, b, c, d);
+  std::copy(a.begin(), a.end(), t1);
+  std::copy(b.begin(), b.end(), t2);
+  std::copy(c.begin(), c.end(), S21);
+  std::copy(d.begin(), d.end(), S22);
+  return SMC_OK;
+}
+
+const char *smc_last_error(smc_handle *h) {
+  if (!h) return "null handle";
+  return h->err.c_str();
+}
+
+}  // extern "C"

@@ -1,0 +1,125 @@
+// Time-integration kernels: the SDC node update (Sec. 3.1, eq. expsdc) as a
+// linear combination of state and right-hand-side arrays, and the mode-1
+// multirate fine-node chain (Sec. 3.2, eq. mrupdate) in which every cell
+// advances through the reaction substeps of one coarse interval on its own.
+#include "chem.cuh"
+#include "smc_internal.h"
+
+namespace smc {
+
+static int grid_for(long long n, int block) {
+  long long b = (n + block - 1) / block;
+  const long long cap = 152LL * 64;
+  if (b > cap) b = cap;
+  if (b < 1) b = 1;
+  return (int)b;
+}
+
+// out = in + sum_j c_j src_j  (elementwise; in may alias out)
+__global__ void __launch_bounds__(256) k_combo(const double *in, double *out, const Combo cb,
+                                               long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    double acc = in[i];
+    for (int j = 0; j < cb.nsrc; ++j) acc += cb.c[j] * cb.src[j][i];
+    out[i] = acc;
+  }
+}
+
+void launch_combo(const double *in, double *out, const Combo &cb, long long n, cudaStream_t st) {
+  k_combo<<<grid_for(n, 256), 256, 0, st>>>(in, out, cb, n);
+}
+
+// Reaction right-hand side f2 at one cell from its conserved state.
+__device__ __forceinline__ bool cell_reactions(const DevState &s, const double *Uc, double *f2,
+                                               unsigned &flag) {
+  const Mech &m = *s.mech;
+  const int ns = s.ns;
+  const double rho = Uc[0];
+  const double invrho = 1.0 / rho;
+  const double u = Uc[1] * invrho, v = Uc[2] * invrho, w = Uc[3] * invrho;
+  double Y[SMC_MAX_NS];
+  for (int k = 0; k < ns; ++k) Y[k] = Uc[5 + k] * invrho;
+  const double e = Uc[4] * invrho - 0.5 * (u * u + v * v + w * w);
+  double T;
+  const bool ok = newton_T(m, Y, e, s.opt.T0, s.opt.tol, s.opt.maxit, T);
+  if (!ok) flag |= ST_NONCONV;
+  if (!(rho > 0.0) || !(T > 0.0)) flag |= ST_NONPHYS;
+  if (!isfinite(rho) || !isfinite(T)) flag |= ST_NONFINITE;
+  if (s.opt.reactions && m.nr > 0) {
+    production_rates(m, s.rx, rho, T, Y, f2);
+  } else {
+    for (int k = 0; k < ns; ++k) f2[k] = 0.0;
+  }
+  return ok;
+}
+
+__global__ void __launch_bounds__(128) k_chem_only(const DevState s, const double *__restrict__ U,
+                                                   double *__restrict__ F2) {
+  const int ns = s.ns, nv = s.nv;
+  const long long NI = s.ncells;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < NI;
+       i += (long long)gridDim.x * blockDim.x) {
+    double Uc[5 + SMC_MAX_NS], f2[SMC_MAX_NS];
+    for (int c = 0; c < nv; ++c) Uc[c] = U[(size_t)c * NI + i];
+    unsigned flag = 0;
+    cell_reactions(s, Uc, f2, flag);
+    if (flag) atomicOr(s.status, flag);
+    for (int k = 0; k < ns; ++k) F2[(size_t)k * NI + i] = f2[k];
+  }
+}
+
+void launch_chem_only(const DevState &s, const double *U, double *F2, cudaStream_t st) {
+  k_chem_only<<<grid_for(s.ncells, 128), 128, 0, st>>>(s, U, F2);
+}
+
+// Fine substeps q = q0 .. q0+nsub-1 of eq. mrupdate for every cell:
+//   U_{q+1} = U_q + dt_q [f1(U^{k+1}_p) - f1(U^k_p)] + dt_q [f2(U^{k+1}_q) - f2(U^k_q)]
+//             + dt (S22 F2^k)_q + dt (S21 F1^k)_q
+// f1 is frozen at the coarse node p on the left; f2 (reactions, species
+// components only) is evaluated at every fine node.
+__global__ void __launch_bounds__(128) k_fine_chain(const DevState s, const double *__restrict__ Uin,
+                                                    double *__restrict__ Uout, const FineChain fc) {
+  const int ns = s.ns, nv = s.nv, M1 = fc.M1;
+  const long long NI = s.ncells;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < NI;
+       i += (long long)gridDim.x * blockDim.x) {
+    double Uc[5 + SMC_MAX_NS], f2[SMC_MAX_NS];
+    for (int c = 0; c < nv; ++c) Uc[c] = Uin[(size_t)c * NI + i];
+    unsigned flag = 0;
+    for (int sidx = 0; sidx < fc.nsub; ++sidx) {
+      if (sidx > 0 || fc.eval_first) {
+        cell_reactions(s, Uc, f2, flag);
+        for (int k = 0; k < ns; ++k) fc.F2new[sidx][(size_t)k * NI + i] = f2[k];
+      } else {
+        for (int k = 0; k < ns; ++k) f2[k] = fc.F2old[0][(size_t)k * NI + i];
+      }
+      const double dq = fc.dtq[sidx];
+      for (int c = 0; c < nv; ++c) {
+        const size_t o = (size_t)c * NI + i;
+        double acc = dq * (fc.F1new_p[o] - fc.F1old_p[o]);
+        for (int j = 0; j <= M1; ++j) acc += fc.s21[sidx][j] * fc.F1old[j][o];
+        if (c >= 5) {
+          const int k = c - 5;
+          const size_t ok = (size_t)k * NI + i;
+          acc += dq * (f2[k] - fc.F2old[sidx][ok]);
+          for (int t = 0; t <= fc.nsub; ++t) acc += fc.s22[sidx][t] * fc.F2old[t][ok];
+        }
+        Uc[c] += acc;
+      }
+    }
+    if (fc.eval_last) {
+      cell_reactions(s, Uc, f2, flag);
+      for (int k = 0; k < ns; ++k) fc.F2new[fc.nsub][(size_t)k * NI + i] = f2[k];
+    }
+    if (flag) atomicOr(s.status, flag);
+    for (int c = 0; c < nv; ++c) Uout[(size_t)c * NI + i] = Uc[c];
+  }
+}
+
+void launch_fine_chain(const DevState &s, const double *Uin, double *Uout, const FineChain &fc,
+                       cudaStream_t st) {
+  k_fine_chain<<<grid_for(s.ncells, 128), 128, 0, st>>>(s, Uin, Uout, fc);
+}
+
+}  // namespace smc

@@ -1,0 +1,150 @@
+// Internal data structures shared by the kernels and the host orchestration.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "smc.h"
+
+#define SMC_MAX_NS 64
+#define SMC_MAX_SIDE 4        // species per reaction side
+#define SMC_GHOST 4           // ghost cells per side (8th-order stencils)
+
+namespace smc {
+
+constexpr double kRu = 8.31446261815324e7;     // erg/(mol K)
+constexpr double kRc = 1.98720425864083;       // cal/(mol K)
+constexpr double kPatm = 1.01325e6;            // dyn/cm^2
+
+// Device-resident mechanism tables (one per handle).
+struct Mech {
+  int ns, nr;
+  double Ru_W[SMC_MAX_NS];        // R_u / W_k
+  double W[SMC_MAX_NS];
+  double invW[SMC_MAX_NS];
+  double invLe[SMC_MAX_NS];
+  double cp[SMC_MAX_NS][5];       // cp/R = c0 + c1 T + ... + c4 T^4
+  double hT[SMC_MAX_NS][6];       // h/R  = a6 + T (a1 + T (a2/2 + ...))
+  double sR[SMC_MAX_NS][6];       // s/R  = a1 ln T + a7 + T (a2 + T (a3/2 + ...)) : {a1, a7, a2, a3/2, a4/3, a5/4}
+  double eta_ref, inv_T_ref, eta_exp, inv_Pr;
+};
+
+struct Reaction {
+  double lnA, b, Ea_R;            // Ea / R_c (K)
+  double dnu;                     // sum_k nu''_k - nu'_k
+  int nf, nr_;                    // species on each side
+  int fk[SMC_MAX_SIDE], fc[SMC_MAX_SIDE];
+  int rk[SMC_MAX_SIDE], rc[SMC_MAX_SIDE];
+};
+
+// Geometry of one box in the ghosted (Q) and interior (U) layouts.
+struct Box {
+  int nx, ny, nz;
+  int gx, gy, gz;                 // ghosted extents n + 8
+  long long off_g, off_i;         // first ghosted / interior cell
+};
+
+// One thread's share of a stencil direction: a segment of one grid line.
+struct LineItem {
+  long long g0;                   // ghosted index of the first cell of the segment
+  long long i0;                   // interior index of that cell
+  int sg, si;                     // strides along the line (ghosted, interior)
+  int len;                        // cells in the segment
+  int pad;
+};
+
+// Runtime options passed to the kernels by value.
+struct Opts {
+  int mode;                       // 0 correction velocity, 1 reference species
+  int ref;
+  int reactions;
+  int maxit;
+  double tol, T0, xi_ratio;
+};
+
+// Stencil coefficients, per direction, scaled by 1/h^2 (narrow) or 1/h (D).
+struct Coef {
+  double M[3][8][8];
+  double D[3][4];
+  double S[8];                    // unused padding for alignment
+};
+
+// Q field indices (ghosted primitive / coefficient scratch).
+enum {
+  Q_U = 0, Q_V, Q_W, Q_T, Q_P, Q_RHO, Q_RHOH, Q_C43, Q_ETA, Q_C23, Q_LAM,
+  Q_HMIX, Q_AP, Q_SB, Q_KX, Q_KY, Q_KZ, Q_NBASE
+};
+// species blocks start at Q_NBASE: Y, X, rhoY, rhoD, rhoD*h', B
+inline __host__ __device__ int qY(int ns) { return Q_NBASE; }
+inline __host__ __device__ int qX(int ns) { return Q_NBASE + ns; }
+inline __host__ __device__ int qRY(int ns) { return Q_NBASE + 2 * ns; }
+inline __host__ __device__ int qRD(int ns) { return Q_NBASE + 3 * ns; }
+inline __host__ __device__ int qRDH(int ns) { return Q_NBASE + 4 * ns; }
+inline __host__ __device__ int qB(int ns) { return Q_NBASE + 5 * ns; }
+inline __host__ __device__ int nQ(int ns) { return Q_NBASE + 6 * ns; }
+
+// Device status bits.
+enum : unsigned { ST_NONCONV = 1u, ST_NONPHYS = 2u, ST_NONFINITE = 4u };
+
+// Host-side quadrature (Gauss-Lobatto nodes, Lagrange integration matrices).
+void lobatto_nodes(int n, std::vector<double> &x);
+void node_to_node_matrix(const std::vector<double> &nodes, std::vector<double> &S);
+void multirate_matrices(int coarse, int fine, std::vector<double> &t1, std::vector<double> &t2,
+                        std::vector<double> &S21, std::vector<double> &S22);
+
+// Kernel launchers (kernels_*.cu).
+struct DevState {
+  int ns, nv, nq, nboxes;
+  long long ncells, nghost;
+  const Mech *mech;
+  const Reaction *rx;
+  const Coef *hcoef;               // host copy (read by the launchers only)
+  const Box *boxes;
+  const int *gmap;                // ghosted cell -> interior index of its periodic image
+  const long long *imap;          // interior cell -> ghosted index
+  const LineItem *lines[3];
+  long long nlines[3];
+  double *Q;                      // [nq][nghost]
+  double *G;                      // [9][nghost] velocity gradients D_e u_c
+  double *divacc;                 // [ncells] sum_k narrow species divergence
+  unsigned *status;
+  Opts opt;
+};
+
+void launch_prim(const DevState &s, const double *U, cudaStream_t st);
+void launch_grad(const DevState &s, cudaStream_t st);
+void launch_march(const DevState &s, int dir, double *dUdt, int first, cudaStream_t st);
+void launch_final(const DevState &s, double *dUdt, int transport, int chemistry, cudaStream_t st);
+void launch_prim_to_cons(const DevState &s, const double *prim, double *U, cudaStream_t st);
+
+// out = in + sum_i c[i] * src[i] over n doubles (n = nv * ncells)
+struct Combo {
+  int nsrc;
+  double c[12];
+  const double *src[12];
+};
+void launch_combo(const double *in, double *out, const Combo &cb, long long n, cudaStream_t st);
+
+// Multirate fine-node chain over one coarse interval (eq. mrupdate).  Fine
+// substeps q = q0 .. q0+nsub-1 lie in one Gauss-Lobatto group whose nodes are
+// q0 .. q0+nsub (type (b): one group per coarse interval).
+struct FineChain {
+  int q0, nsub, p, M1;
+  double dtq[8];                  // dt * (t2[q+1] - t2[q])
+  double s21[8][5];               // dt * S21[q][j], j over coarse nodes
+  double s22[8][9];               // dt * S22[q][q0 + t], t over the group's nodes
+  const double *F1new_p, *F1old_p;   // coarse F at node p (new / old sweep), NV comps
+  const double *F1old[5];            // old coarse F at every coarse node
+  const double *F2old[9];            // old fine F at the group's nodes, ns comps
+  double *F2new[9];                  // new fine F at the group's nodes
+  int eval_first;                 // evaluate f2 at node q0 (false only for q0 = 0)
+  int eval_last;                  // evaluate f2 at node q0 + nsub after the last substep
+};
+void launch_fine_chain(const DevState &s, const double *U0, double *U, const FineChain &fc,
+                       cudaStream_t st);
+void launch_chem_only(const DevState &s, const double *U, double *F2, cudaStream_t st);
+
+}  // namespace smc

@@ -1,0 +1,178 @@
+"""Parity of the CUDA right-hand side with the FP64 oracle (element by
+element, max-norm relative error per component <= 1e-12)."""
+import numpy as np
+import pytest
+
+from oracle import rhs as orhs
+from oracle import thermo
+from paper_1309_7327_gb300 import synth
+
+from util import oracle_rhs, relerr, state
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-12
+
+
+@pytest.fixture(scope="module")
+def smc():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1309_7327_gb300 import smc as S
+    return S
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to("cuda:0")
+
+
+def gpu_rhs(S, wl, U, **options):
+    with S.Smc(wl.grid, wl.mech, options) as h:
+        Ud = dev(U)
+        F = torch.empty_like(Ud)
+        h.rhs(Ud, F)
+        h.synchronize()
+        return F.cpu().numpy()
+
+
+def test_prim_to_cons(smc):
+    wl, U, U_g = state("c2", n=16)
+    with smc.Smc(wl.grid, wl.mech) as h:
+        P = dev(wl.prim)
+        out = torch.empty_like(P)
+        h.prim_to_cons(P, out)
+        h.synchronize()
+    assert relerr(out.cpu().numpy(), U).max() < 1e-14
+
+
+@pytest.mark.parametrize("seed", [1, 2])
+def test_rhs_c1(smc, seed):
+    wl, U, U_g = state("c1", seed=seed, p_amp=0.03)
+    err = relerr(gpu_rhs(smc, wl, U), oracle_rhs(wl, U_g))
+    assert err.max() < TOL, err
+
+
+def test_rhs_c1_reference_species_mode(smc):
+    wl, U, U_g = state("c1", seed=3, p_amp=0.03)
+    got = gpu_rhs(smc, wl, U, diffusion_mode=1)
+    err = relerr(got, oracle_rhs(wl, U_g, mode="ref"))
+    assert err.max() < TOL, err
+
+
+def test_rhs_options_bulk_viscosity_and_stencil_parameters(smc):
+    wl, U, U_g = state("c1", seed=4, p_amp=0.03)
+    from oracle import stencil as ost
+    got = gpu_rhs(smc, wl, U, xi_ratio=0.6, m47=float(ost.M47_OPT), m48=float(ost.M48_OPT))
+    err = relerr(got, oracle_rhs(wl, U_g, xi_ratio=0.6, m47=ost.M47_OPT, m48=ost.M48_OPT))
+    assert err.max() < TOL, err
+
+
+def test_rhs_no_reactions(smc):
+    wl, U, U_g = state("c1", seed=5)
+    err = relerr(gpu_rhs(smc, wl, U, reactions=0), oracle_rhs(wl, U_g, reactions=False))
+    assert err.max() < TOL, err
+
+
+@pytest.mark.parametrize("segment", [16, 5, 64])
+def test_rhs_ragged_box_nine_species(smc, segment):
+    """A 20 x 24 x 28 box (segments, ragged tails), 9 species / 21 reactions."""
+    wl = synth.workload("c2", seed=2, n=8)
+    grid = synth.single_box((20, 24, 28), (0.1 / 20, 0.1 / 24, 0.1 / 28))
+    g = synth.bump_fields(grid, 9, 5)
+    U_g = thermo.conserved(g, wl.mech.nasa7, wl.mech.W)
+    wl.grid = grid
+    U = synth.global_to_boxes(grid, U_g)
+    err = relerr(gpu_rhs(smc, wl, U, segment=segment), oracle_rhs(wl, U_g))
+    assert err.max() < TOL, err
+
+
+def test_rhs_multibox_21_species(smc):
+    """Eight uneven boxes tiling a periodic domain (ghost cells gathered from
+    neighbouring boxes), 21 species / 84 reactions."""
+    wl = synth.workload("c4", seed=3, n=12)
+    assert wl.grid.nboxes == 8
+    prim_g = synth.boxes_to_global(wl.grid, wl.prim)
+    U_g = thermo.conserved(prim_g, wl.mech.nasa7, wl.mech.W)
+    U = synth.global_to_boxes(wl.grid, U_g)
+    err = relerr(gpu_rhs(smc, wl, U), oracle_rhs(wl, U_g))
+    assert err.max() < TOL, err
+
+
+def test_rhs_tiny_box_single_species(smc):
+    """Degenerate case: one species, no reactions, a 5 x 6 x 7 box smaller
+    than two stencil widths (ghost cells wrap several times)."""
+    mech = synth.make_mechanism(1, 0, 1)
+    grid = synth.single_box((5, 6, 7), (0.01, 0.012, 0.014))
+    prim = synth.smooth_fields(grid, 1, 3, p_amp=0.05)
+    U_g = thermo.conserved(prim, mech.nasa7, mech.W)
+    U = synth.global_to_boxes(grid, U_g)
+
+    class W:
+        pass
+    wl = W()
+    wl.grid, wl.mech = grid, mech
+    err = relerr(gpu_rhs(smc, wl, U), oracle_rhs(wl, U_g))
+    assert err.max() < TOL, err
+
+
+def test_rhs_host_pointers_match_device(smc):
+    wl, U, U_g = state("c1", seed=6, p_amp=0.03)
+    with smc.Smc(wl.grid, wl.mech) as h:
+        F = np.empty_like(U)
+        h.rhs(U, F)
+        Fd = torch.empty_like(dev(U))
+        h.rhs(dev(U), Fd)
+        h.synchronize()
+    assert np.array_equal(F, Fd.cpu().numpy())
+
+
+def _sample_cells(rng, grid, k):
+    nx, ny, nz = grid.domain
+    cells = [(0, 0, 0), (nz - 1, ny - 1, nx - 1)]
+    for _ in range(k):
+        cells.append((int(rng.integers(nz)), int(rng.integers(ny)), int(rng.integers(nx))))
+    return cells
+
+
+@pytest.mark.parametrize("name", ["c2", "c4"])
+def test_rhs_full_size_sampled_cells(smc, name):
+    """Full-size configurations, in the launch configuration the benchmark
+    uses, checked at sampled cells that the oracle evaluates one by one."""
+    wl = synth.workload(name, seed=1)
+    g = wl.grid
+    prim_g = synth.boxes_to_global(g, wl.prim)
+    U_g = thermo.conserved(prim_g, wl.mech.nasa7, wl.mech.W)
+    U = synth.global_to_boxes(g, U_g)
+    F = synth.boxes_to_global(g, gpu_rhs(smc, wl, U))
+    cells = _sample_cells(np.random.default_rng(0), g, 10)
+    ref = orhs.rhs_at(U_g, cells, wl.mech, g.dx)
+    got = np.stack([F[:, z, y, x] for z, y, x in cells], axis=1)
+    full_scale = np.abs(F).reshape(F.shape[0], -1).max(axis=1)
+    err = np.abs(got - ref).max(axis=1) / full_scale
+    assert err.max() < TOL, err
+
+
+def test_nan_input_reports_nonphysical(smc):
+    wl, U, U_g = state("c1", seed=1)
+    U = U.copy()
+    U[4, 17] = np.nan
+    with smc.Smc(wl.grid, wl.mech) as h:
+        F = np.empty_like(U)
+        with pytest.raises(smc.SmcError) as e:
+            h.rhs(U, F)
+        assert e.value.status in (smc.SMC_ERR_NONPHYSICAL, smc.SMC_ERR_NONCONVERGED)
+        # the handle stays usable
+        h.rhs(np.ascontiguousarray(state("c1", seed=1)[1]), F)
+
+
+def test_bad_arguments(smc):
+    wl, U, U_g = state("c1", seed=1)
+    with smc.Smc(wl.grid, wl.mech) as h:
+        with pytest.raises(smc.SmcError) as e:
+            h.sdc_step(dev(U), 1e-9, nodes=4)
+        assert e.value.status == smc.SMC_ERR_ARG
+        with pytest.raises(smc.SmcError):
+            h.sdc_step(dev(U), -1.0)
+        with pytest.raises(smc.SmcError):
+            h.set_option("diffusion_mode", 3)

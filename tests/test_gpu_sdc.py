@@ -1,0 +1,123 @@
+"""Parity of the CUDA SDC and multirate-SDC steps with the oracle's
+(Sec. 3.1 eq. expsdc, Sec. 3.2 eq. mrupdate), and the evaluation counts."""
+import numpy as np
+import pytest
+
+from oracle import rhs as orhs
+from oracle import sdc as osdc
+from paper_1309_7327_gb300 import synth
+
+from util import relerr, state
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+# The state changes by a small fraction per step, so compare the increments
+# U_new - U_0 (their relative error carries the RHS error at ~1e-12 plus the
+# rounding of U at ~1e-16 |U| / |dU|).
+TOL = 1e-10
+
+
+@pytest.fixture(scope="module")
+def smc():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1309_7327_gb300 import smc as S
+    return S
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to("cuda:0")
+
+
+def oracle_f(wl, part="full"):
+    def f(u, t=0.0):
+        tr, ch = orhs.rhs_periodic(u, wl.mech, wl.grid.dx, parts=True)
+        return {"full": tr + ch, "transport": tr, "chem": ch}[part]
+    return f
+
+
+@pytest.mark.parametrize("nodes,sweeps", [(3, 4), (5, 2)])
+def test_sdc_step_c1(smc, nodes, sweeps):
+    wl, U, U_g = state("c1", seed=1, p_amp=0.03)
+    dt = wl.dt
+    with smc.Smc(wl.grid, wl.mech) as h:
+        Ud = dev(U)
+        h.sdc_step(Ud, dt, nodes=nodes, sweeps=sweeps)
+        h.synchronize()
+        st = h.stats()
+        U1 = Ud.cpu().numpy()
+    ref, _, nev = osdc.sdc_step(U_g, oracle_f(wl), dt, nodes=nodes, sweeps=sweeps)
+    ref = synth.global_to_boxes(wl.grid, ref)
+    assert st["n_rhs"] == nev == sweeps * (nodes - 1) + 1
+    err = relerr(U1 - U, ref - U)
+    assert err.max() < TOL, err
+
+
+def test_two_steps_recycle_f0(smc):
+    """The second step reuses f(U_M) of the first (N_evals = K M per step)."""
+    wl, U, U_g = state("c1", seed=2, p_amp=0.03)
+    dt = wl.dt
+    with smc.Smc(wl.grid, wl.mech) as h:
+        Ud = dev(U)
+        h.sdc_step(Ud, dt)
+        h.sdc_step(Ud, dt)
+        h.synchronize()
+        assert h.stats()["n_rhs"] == 2 * 8 + 1
+        U2 = Ud.cpu().numpy()
+    f = oracle_f(wl)
+    u, F, _ = osdc.sdc_step(U_g, f, dt)
+    u, F, _ = osdc.sdc_step(u, f, dt, F0=F)
+    ref = synth.global_to_boxes(wl.grid, u)
+    err = relerr(U2 - U, ref - U)
+    assert err.max() < TOL, err
+
+
+def test_sdc_conserves_mass_and_momentum(smc):
+    """Periodic flux form: sum over cells of rho and rho u is unchanged."""
+    wl, U, U_g = state("c1", seed=3)
+    with smc.Smc(wl.grid, wl.mech) as h:
+        Ud = dev(U)
+        for _ in range(3):
+            h.sdc_step(Ud, wl.dt)
+        h.synchronize()
+        U3 = Ud.cpu().numpy()
+    for c in range(4):
+        scale = np.abs(U[c]).sum()
+        assert abs(U3[c].sum() - U[c].sum()) <= 1e-13 * scale
+
+
+def test_host_pointer_step_matches_device(smc):
+    wl, U, U_g = state("c1", seed=4)
+    with smc.Smc(wl.grid, wl.mech) as h:
+        Uh = U.copy()
+        h.sdc_step(Uh, wl.dt)
+    with smc.Smc(wl.grid, wl.mech) as h:
+        Ud = dev(U)
+        h.sdc_step(Ud, wl.dt)
+        h.synchronize()
+    assert np.array_equal(Uh, Ud.cpu().numpy())
+
+
+@pytest.mark.parametrize("fine", [5, 3])
+def test_mrsdc_step_multibox(smc, fine):
+    """Mode-1 multirate step (3 coarse / `fine` fine nodes per coarse
+    interval) on 8 uneven boxes, 21 species."""
+    wl = synth.workload("c4", seed=2, n=10)
+    from oracle import thermo
+    prim_g = synth.boxes_to_global(wl.grid, wl.prim)
+    U_g = thermo.conserved(prim_g, wl.mech.nasa7, wl.mech.W)
+    U = synth.global_to_boxes(wl.grid, U_g)
+    dt = wl.dt
+    with smc.Smc(wl.grid, wl.mech) as h:
+        Ud = dev(U)
+        h.sdc_step(Ud, dt, nodes=3, sweeps=4, reaction_substeps=fine)
+        h.synchronize()
+        st = h.stats()
+        U1 = Ud.cpu().numpy()
+    ref, _, _, n1, n2 = osdc.mrsdc_step(U_g, oracle_f(wl, "transport"), oracle_f(wl, "chem"),
+                                        dt, coarse=3, fine=fine, sweeps=4)
+    ref = synth.global_to_boxes(wl.grid, ref)
+    assert (st["n_rhs"], st["n_react"]) == (n1, n2) == (4 * 2 + 1, 4 * 2 * (fine - 1) + 1)
+    err = relerr(U1 - U, ref - U)
+    assert err.max() < TOL, err
