@@ -44,6 +44,9 @@ def parse():
     ap.add_argument("--workload", default="c4")
     ap.add_argument("--precision", default="fp64", choices=["fp64"])
     ap.add_argument("--seed", type=int, default=1)
+    ap.add_argument("--n", type=int, default=None,
+                    help="smaller instance of the workload (profiling captures)")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
     return ap.parse_args()
 
 
@@ -127,10 +130,12 @@ class ClockSampler:
 def march_flops_per_cell(ns: int, mode: int = 0) -> float:
     """FP64 flops one stencil-direction kernel (k_march) spends per cell,
     counted from its source (an FMA is 2 flops): narrow-stencil face fluxes
-    508 + 143 ns, flux differences 4 + 2 ns, convective + mixed viscous D
-    225 + 21 ns, correction velocity 27 + 28 ns, accumulation 5 + ns."""
+    490 + 134 ns (difference-first: 87 per M u, 81 per M^T a, 20 per
+    difference dot, 15 per plain dot), flux differences 4 + 2 ns, convective
+    + mixed viscous D 225 + 21 ns, correction velocity 27 + 28 ns,
+    accumulation 5 + ns."""
     vc = 27 + 28 * ns if mode == 0 else 0
-    return 508 + 143 * ns + 4 + 2 * ns + 225 + 21 * ns + vc + 5 + ns
+    return 490 + 134 * ns + 4 + 2 * ns + 225 + 21 * ns + vc + 5 + ns
 
 
 def measured_peaks():
@@ -216,7 +221,7 @@ def main():
     __graft_entry__.build()
     from paper_1309_7327_gb300 import smc, synth
 
-    wl = synth.workload(args.workload, seed=args.seed)
+    wl = synth.workload(args.workload, seed=args.seed, n=args.n)
     nodes, sweeps, rsub = wl.nodes, wl.sweeps, wl.reaction_substeps
     M1 = nodes - 1
     evals_per_step = sweeps * M1
@@ -310,13 +315,13 @@ def main():
            "h2d_bytes_per_step": nv * ncells * 8, "d2h_bytes_per_step": nv * ncells * 8}
 
     if rank == 0:
-        cpu = cpu_baseline(wl) if world == 1 else None
+        cpu = cpu_baseline(wl) if (world == 1 and not args.no_cpu) else None
         line = {
             "metric": "Mcell-RHS/s (21 species)", "value": value, "unit": "Mcell-RHS/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": args.workload, "boxes": wl.grid.nboxes, "cells": ncells,
+            "config": {"workload": args.workload + (f" (n={args.n})" if args.n else ""), "boxes": wl.grid.nboxes, "cells": ncells,
                        "species": wl.mech.ns, "reactions": wl.mech.nr,
                        "integrator": (f"MRSDC {nodes} coarse / {rsub} fine GL, {sweeps} sweeps"
                                       if rsub >= 2 else f"SDC {nodes} GL, {sweeps} sweeps"),

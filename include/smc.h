@@ -80,6 +80,10 @@ typedef struct {
  * Transport (the paper uses EGLIB; this library uses the model below):
  *   eta = eta_ref (T/T_ref)^eta_exp, lambda = cp eta / Pr,
  *   rho D_k = lambda / (cp Le_k), bulk viscosity xi = xi_ratio * eta.
+ * Limits checked by smc_create (SMC_ERR_ARG otherwise): every reaction
+ * conserves mass (sum_k nu_k W_k = 0 to 1e-9), has at most 4 species and 3
+ * molecules per side; cp > 0 and the species' g/RT spread over less than
+ * 400 on 200..3500 K (the FP64 range of the rate evaluation).
  * All arrays are host memory, copied by smc_create. */
 typedef struct {
   int nspecies;              /* 1 .. 64 */
@@ -142,10 +146,11 @@ typedef struct {
   double kernel_ms[SMC_NKERNELS];     /* summed device time per class (profiling on) */
 } smc_stats;
 
-/* Create a handle: validates the mechanism (element/mass balance sum_k
- * nu_k W_k = 0 per reaction, cp > 0 on 200..3500 K) and the grid, uploads
- * constants and builds the ghost-cell gather maps.  *out receives the
- * handle.  The current CUDA device is used. */
+/* Create a handle: validates the mechanism (limits above) and the grid,
+ * uploads constants and builds the ghost-cell gather maps.  *out receives
+ * the handle.  The current CUDA device is used.  On failure *out may still
+ * receive a handle that holds the error message (smc_last_error); pass it
+ * to smc_destroy. */
 smc_status smc_create(const smc_grid *grid, const smc_mechanism *mech,
                       const smc_bc *bc, smc_handle **out);
 

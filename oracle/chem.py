@@ -26,7 +26,7 @@ def production_rates(rho, T, Y, mech) -> np.ndarray:
     shape = (-1,) + (1,) * T.ndim
     c = rho[None] * Y / W.reshape(shape)
     g = h_RT(mech.nasa7, T) - s_R(mech.nasa7, T)
-    wdot = np.zeros((ns,) + T.shape)
+    wdot = np.zeros((ns,) + T.shape, dtype=T.dtype)
     for r in range(mech.A.shape[0]):
         nf = mech.nu_f[r]
         nr = mech.nu_r[r]

@@ -91,11 +91,11 @@ def rhs_ghosted(Ug: np.ndarray, mech, dx, opt: Options | None = None,
     c23 = xi - 2.0 / 3.0 * eta
     hmix = np.sum(Y * h, axis=0)
     B = rhoD * (X - Y) / p[None]
-    M = stencil.to_float(stencil.narrow8_exact(opt.m47, opt.m48))
+    M = stencil.to_float(stencil.narrow8_exact(opt.m47, opt.m48), Ug.dtype)
 
     interior = _inner(_inner(_inner(Ug, [0]), [1]), [2]).shape
-    out = np.zeros(interior)
-    Nsum = np.zeros((ns,) + interior[1:])
+    out = np.zeros(interior, dtype=Ug.dtype)
+    Nsum = np.zeros((ns,) + interior[1:], dtype=Ug.dtype)
     ref = opt.ref % ns
 
     for d in range(3):
@@ -168,7 +168,7 @@ def rhs_ghosted(Ug: np.ndarray, mech, dx, opt: Options | None = None,
         out[5:] += Yi * divVc[None]
         out[4] += hi * divVc
 
-    ch = np.zeros(interior)
+    ch = np.zeros(interior, dtype=Ug.dtype)
     if opt.reactions and mech.A.shape[0] > 0:
         ri = _inner(_inner(_inner(rho, [0]), [1]), [2])
         Ti = _inner(_inner(_inner(T, [0]), [1]), [2])
@@ -200,7 +200,7 @@ def patch(U: np.ndarray, z: int, y: int, x: int) -> np.ndarray:
 
 def rhs_at(U: np.ndarray, cells, mech, dx, opt: Options | None = None) -> np.ndarray:
     """dU/dt of a periodic field at a list of (z, y, x) cells, one by one."""
-    out = np.empty((U.shape[0], len(cells)))
+    out = np.empty((U.shape[0], len(cells)), dtype=U.dtype)
     for i, (z, y, x) in enumerate(cells):
         out[:, i] = rhs_ghosted(patch(U, z, y, x), mech, dx, opt)[:, 0, 0, 0]
     return out

@@ -98,8 +98,11 @@ def narrow6_exact(m36=M36_SMC):
     return M
 
 
-def to_float(M) -> np.ndarray:
-    return np.array([[float(v) for v in row] for row in M], dtype=np.float64)
+def to_float(M, dtype=np.float64) -> np.ndarray:
+    """Exact rationals -> floating point (float64, or np.longdouble for the
+    extended-precision check of ill-conditioned components)."""
+    t = np.dtype(dtype).type
+    return np.array([[t(v.numerator) / t(v.denominator) for v in row] for row in M], dtype=dtype)
 
 
 def _take(f: np.ndarray, axis: int, start: int, length: int) -> np.ndarray:
@@ -111,9 +114,10 @@ def _take(f: np.ndarray, axis: int, start: int, length: int) -> np.ndarray:
 def D(f: np.ndarray, axis: int, h: float, g: int = 4) -> np.ndarray:
     """8th-order centred first derivative along ``axis``; trims g ghosts."""
     n = f.shape[axis] - 2 * g
-    out = np.zeros(_take(f, axis, g, n).shape)
+    t = f.dtype.type
+    out = np.zeros(_take(f, axis, g, n).shape, dtype=f.dtype)
     for k, c in enumerate(D8, start=1):
-        out = out + float(c) * (_take(f, axis, g + k, n) - _take(f, axis, g - k, n))
+        out = out + (t(c.numerator) / t(c.denominator)) * (_take(f, axis, g + k, n) - _take(f, axis, g - k, n))
     return out / h
 
 
@@ -127,7 +131,7 @@ def narrow(a: np.ndarray, u: np.ndarray, axis: int, h: float, M: np.ndarray,
     s = M.shape[0] // 2
     n = a.shape[axis] - 2 * g
     nf = n + 1                       # faces -1/2 .. n-1/2
-    H = np.zeros(_take(a, axis, 0, nf).shape)
+    H = np.zeros(_take(a, axis, 0, nf).shape, dtype=np.result_type(a, u, M))
     # face f (= i+1/2 with i = f-1) sits between ghosted indices g+f-1 and g+f
     for mi in range(2 * s):
         m = mi - s + 1

@@ -70,7 +70,7 @@ def temperature(nasa, W, Y: np.ndarray, e: np.ndarray, T0: float = 1000.0,
     Returns (T, converged mask).  Every cell iterates from T0; a cell stops
     changing once its own step satisfied |dT| <= tol * T.
     """
-    T = np.full(e.shape, float(T0))
+    T = np.full(e.shape, T0, dtype=e.dtype)
     done = np.zeros(e.shape, dtype=bool)
     for _ in range(maxit):
         f = np.sum(Y * e_k(nasa, W, T), axis=0) - e
@@ -112,7 +112,7 @@ def conserved(prim: np.ndarray, nasa, W) -> np.ndarray:
     Wmix_inv = np.sum(Y / W.reshape((-1,) + (1,) * T.ndim), axis=0)
     rho = p / (R_U * T * Wmix_inv)
     e = np.sum(Y * e_k(nasa, W, T), axis=0)
-    U = np.empty((5 + ns,) + T.shape)
+    U = np.empty((5 + ns,) + T.shape, dtype=T.dtype)
     U[0] = rho
     U[1:4] = rho * vel
     U[4] = rho * (e + 0.5 * np.sum(vel ** 2, axis=0))

@@ -508,6 +508,23 @@ smc_status smc_create(const smc_grid *grid, const smc_mechanism *mech, const smc
   }
   if (!(mech->eta_ref > 0) || !(mech->T_ref > 0) || !(mech->Pr > 0))
     return bail(fail(h, SMC_ERR_ARG, "transport parameters must be positive"));
+  M.inv_ns = 1.0 / ns;
+  for (int j = 0; j < 64; ++j) M.exp2tab[j] = (double)exp2l((long double)j / 64.0L);
+  for (int i = 0; i <= 100; ++i) {
+    // the production-rate evaluation needs the species' g/RT to spread over
+    // less than 400 (see production_rates)
+    const double T = 200.0 + 33.0 * i, lnT = log(T);
+    double gmin = 1e300, gmax = -1e300;
+    for (int k = 0; k < ns; ++k) {
+      const double *a = mech->nasa7 + 7 * k;
+      const double hRT = a[0] + T * (a[1] / 2 + T * (a[2] / 3 + T * (a[3] / 4 + T * a[4] / 5))) + a[5] / T;
+      const double sR = a[0] * lnT + T * (a[1] + T * (a[2] / 2 + T * (a[3] / 3 + T * a[4] / 4))) + a[6];
+      gmin = std::min(gmin, hRT - sR);
+      gmax = std::max(gmax, hRT - sR);
+    }
+    if (!(gmax - gmin < 400.0))
+      return bail(fail(h, SMC_ERR_ARG, "species Gibbs energies g/RT spread over more than 400"));
+  }
   M.eta_ref = mech->eta_ref;
   M.inv_T_ref = 1.0 / mech->T_ref;
   M.eta_exp = mech->eta_exp;
@@ -540,6 +557,10 @@ smc_status smc_create(const smc_grid *grid, const smc_mechanism *mech, const smc
     }
     if (R.nf == 0 || R.nr_ == 0) return bail(fail(h, SMC_ERR_ARG, "empty reaction side"));
     if (fabs(mass) > 1e-9 * scale) return bail(fail(h, SMC_ERR_ARG, "reaction does not conserve mass"));
+    int mol_f = 0, mol_r = 0;
+    for (int i = 0; i < R.nf; ++i) mol_f += R.fc[i];
+    for (int i = 0; i < R.nr_; ++i) mol_r += R.rc[i];
+    if (mol_f > 3 || mol_r > 3) return bail(fail(h, SMC_ERR_ARG, "more than three molecules on a reaction side"));
     R.dnu = dnu;
   }
   // ---- grid

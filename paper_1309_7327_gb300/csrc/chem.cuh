@@ -5,6 +5,35 @@
 
 namespace smc {
 
+// exp(x) in FP64 by the table-driven method of P. T. P. Tang (ACM TOMS 15,
+// 1989): x = (64 k + j) ln2/64 + r with |r| <= ln2/128, so that
+//   exp(x) = 2^k * 2^(j/64) * exp(r),
+// 2^(j/64) from a 64-entry table and exp(r) - 1 from its Taylor polynomial
+// to r^5 (truncation r^6/720 < 4e-17 relative).  n = 64 k + j is rounded with
+// the 1.5 * 2^52 shift, and 2^k is applied to the exponent field with integer
+// arithmetic.  x is clamped to [-708, 709] (the normal range of the result).
+// About 13 FP64 operations; error within ~1 ulp.
+__device__ __forceinline__ double fast_exp(const Mech &m, double x) {
+  x = fmin(fmax(x, -708.0), 709.0);
+  const double shift = 6755399441055744.0;                 // 1.5 * 2^52
+  const double t = x * 92.33248261689366;                  // 64 / ln 2
+  const double nd = (t + shift) - shift;                   // nearest integer
+  const int n = __double2loint(t + shift);
+  // ln2/64 split: L1 has trailing zero bits so nd * L1 is exact for |n| < 2^18
+  const double L1 = 0.010830424696223417, L2 = 2.572804622327669e-14;
+  const double r = fma(-nd, L2, fma(-nd, L1, x));
+  double q = 1.0 / 120.0;
+  q = fma(q, r, 1.0 / 24.0);
+  q = fma(q, r, 1.0 / 6.0);
+  q = fma(q, r, 0.5);
+  const double p = fma(r * r, q, r);                       // exp(r) - 1
+  const int j = n & 63;
+  const int k = n >> 6;                                    // floor division
+  const double tj = m.exp2tab[j];
+  const double y = fma(tj, p, tj);
+  return __hiloint2double(__double2hiint(y) + (k << 20), __double2loint(y));
+}
+
 // cp/R of species k at T.
 __device__ __forceinline__ double cpR(const Mech &m, int k, double T) {
   const double *c = m.cp[k];
@@ -25,23 +54,33 @@ __device__ __forceinline__ double sR(const Mech &m, int k, double T, double lnT)
 
 // Temperature from the specific internal energy e and mass fractions Y:
 // Newton's method on sum_k Y_k e_k(T) = e, e_k = (R/W_k)(h_k/R - T), from the
-// first guess T0, stopping when |dT| <= tol |T|.  Returns false if maxit steps
-// did not converge.
+// first guess T0, stopping when |dT| <= tol |T|.  The species sums are folded
+// once into the coefficients of one mixture polynomial
+//   e(T) = sum_j H_j T^j - T sum_k Y_k R/W_k,   H_j = sum_k Y_k (R/W_k) hT[k][j],
+// so every iteration costs one Horner evaluation of e and of de/dT = c_v.
+// Returns false if maxit steps did not converge.
 __device__ __forceinline__ bool newton_T(const Mech &m, const double *Y, double e, double T0,
                                          double tol, int maxit, double &Tout) {
   const int ns = m.ns;
-  double yr_sum = 0.0;
-  for (int k = 0; k < ns; ++k) yr_sum += Y[k] * m.Ru_W[k];
+  double H0 = 0.0, H1 = 0.0, H2 = 0.0, H3 = 0.0, H4 = 0.0, H5 = 0.0, yr_sum = 0.0;
+  for (int k = 0; k < ns; ++k) {
+    const double yr = Y[k] * m.Ru_W[k];
+    const double *c = m.hT[k];
+    H0 += yr * c[0];
+    H1 += yr * c[1];
+    H2 += yr * c[2];
+    H3 += yr * c[3];
+    H4 += yr * c[4];
+    H5 += yr * c[5];
+    yr_sum += yr;
+  }
+  H0 -= e;
+  H1 -= yr_sum;
+  const double D2 = 2.0 * H2, D3 = 3.0 * H3, D4 = 4.0 * H4, D5 = 5.0 * H5;
   double T = T0;
   for (int it = 0; it < maxit; ++it) {
-    double f = 0.0, fp = 0.0;
-    for (int k = 0; k < ns; ++k) {
-      const double yr = Y[k] * m.Ru_W[k];
-      f += yr * hR(m, k, T);
-      fp += yr * cpR(m, k, T);
-    }
-    f -= yr_sum * T + e;
-    fp -= yr_sum;
+    const double f = H0 + T * (H1 + T * (H2 + T * (H3 + T * (H4 + T * H5))));
+    const double fp = H1 + T * (D2 + T * (D3 + T * (D4 + T * D5)));
     const double dT = f / fp;
     T -= dT;
     if (fabs(dT) <= tol * fabs(T)) {
@@ -55,34 +94,52 @@ __device__ __forceinline__ bool newton_T(const Mech &m, const double *Y, double 
 
 // rho*omega_k (g/(cm^3 s)) by mass action with reversible Arrhenius rates and
 // equilibrium constants from the Gibbs energies.  wdot[k] is overwritten.
+//
+// With g_k = g_k/(RT), a per-cell shift s (the species mean of g), z_k =
+// c_k exp(g_k - s) and P = (R_u T / p_atm) exp(s), the net rate
+//   q = k_f prod c^nu' - (k_f / K_c) prod c^nu''
+// equals
+//   q = exp(ln k_f - sum_reac nu' (g - s)) (prod_reac z^nu' - P^dnu prod_prod z^nu'')
+// exactly (the exponential factors cancel), which needs one exponential per
+// reaction and one per species instead of two per reaction.  The shift keeps
+// z and the prefactor inside the FP64 range when the species' g spread over
+// less than 400 (checked by smc_create for 200..3500 K) with at most three
+// molecules per reaction side.
 __device__ __forceinline__ void production_rates(const Mech &m, const Reaction *__restrict__ rx,
                                                  double rho, double T, const double *Y,
                                                  double *wdot) {
   const int ns = m.ns;
-  double c[SMC_MAX_NS], g[SMC_MAX_NS];
+  double z[SMC_MAX_NS], g[SMC_MAX_NS];
   const double lnT = log(T);
   const double invT = 1.0 / T;
+  double gs = 0.0;
   for (int k = 0; k < ns; ++k) {
-    c[k] = rho * Y[k] * m.invW[k];
     g[k] = hR(m, k, T) * invT - sR(m, k, T, lnT);   // g_k / (R T)
+    gs += g[k];
+  }
+  gs *= m.inv_ns;
+  for (int k = 0; k < ns; ++k) {
+    g[k] -= gs;
+    z[k] = rho * Y[k] * m.invW[k] * fast_exp(m, g[k]);
     wdot[k] = 0.0;
   }
-  const double ln_patm_RT = log(kPatm / kRu) - lnT;
+  // P^j for j = -4..4
+  const double P1 = T * (kRu / kPatm) * fast_exp(m, gs), Pm1 = 1.0 / P1;
+  const double P2 = P1 * P1, Pm2 = Pm1 * Pm1;
+  const double Ppow[9] = {Pm2 * Pm2, Pm2 * Pm1, Pm2, Pm1, 1.0, P1, P2, P2 * P1, P2 * P2};
   for (int r = 0; r < m.nr; ++r) {
     const Reaction &R = rx[r];
-    const double lnkf = R.lnA + R.b * lnT - R.Ea_R * invT;
-    double sg = 0.0;
-    for (int i = 0; i < R.nr_; ++i) sg += R.rc[i] * g[R.rk[i]];
-    for (int i = 0; i < R.nf; ++i) sg -= R.fc[i] * g[R.fk[i]];
-    // ln Kc = -sum nu g + dnu ln(p_atm / (R T));   ln kr = ln kf - ln Kc
-    const double lnKc = -sg + R.dnu * ln_patm_RT;
-    double fwd = exp(lnkf);
-    double rev = exp(lnkf - lnKc);
-    for (int i = 0; i < R.nf; ++i)
-      for (int j = 0; j < R.fc[i]; ++j) fwd *= c[R.fk[i]];
+    double ex = R.lnA + R.b * lnT - R.Ea_R * invT;
+    double fwd = 1.0, rev = 1.0;
+    for (int i = 0; i < R.nf; ++i) {
+      const int k = R.fk[i];
+      ex -= R.fc[i] * g[k];
+      for (int j = 0; j < R.fc[i]; ++j) fwd *= z[k];
+    }
     for (int i = 0; i < R.nr_; ++i)
-      for (int j = 0; j < R.rc[i]; ++j) rev *= c[R.rk[i]];
-    const double q = fwd - rev;
+      for (int j = 0; j < R.rc[i]; ++j) rev *= z[R.rk[i]];
+    const int dn = (int)R.dnu;
+    const double q = fast_exp(m, ex) * (fwd - Ppow[dn + 4] * rev);
     for (int i = 0; i < R.nf; ++i) wdot[R.fk[i]] -= R.fc[i] * q;
     for (int i = 0; i < R.nr_; ++i) wdot[R.rk[i]] += R.rc[i] * q;
   }

@@ -30,6 +30,8 @@ struct Mech {
   double hT[SMC_MAX_NS][6];       // h/R  = a6 + T (a1 + T (a2/2 + ...))
   double sR[SMC_MAX_NS][6];       // s/R  = a1 ln T + a7 + T (a2 + T (a3/2 + ...)) : {a1, a7, a2, a3/2, a4/3, a5/4}
   double eta_ref, inv_T_ref, eta_exp, inv_Pr;
+  double inv_ns;
+  double exp2tab[64];             // 2^(j/64), j = 0..63 (table of fast_exp)
 };
 
 struct Reaction {

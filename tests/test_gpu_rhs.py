@@ -135,10 +135,31 @@ def _sample_cells(rng, grid, k):
     return cells
 
 
+def conditioning_floor(U_g, cells, mech, dx, scale):
+    """FP64 noise floor of the discrete RHS at the sampled cells: the change of
+    the extended-precision RHS when every input value moves by one unit in
+    the last place (random sign), relative to the component's scale.  Any
+    FP64 evaluation rounds its derived fields (T, X_k, p, ...) at this level,
+    so no FP64 implementation can be closer to the exact result than this."""
+    ref = orhs.rhs_at(U_g.astype(np.longdouble), cells, mech, dx)
+    r = np.random.default_rng(5).choice([-1.0, 1.0], size=U_g.shape)
+    Up = (U_g * (1.0 + r * 2.0 ** -53)).astype(np.longdouble)
+    pert = orhs.rhs_at(Up, cells, mech, dx)
+    return ref.astype(np.float64), np.abs((pert - ref).astype(np.float64)).max(axis=1) / scale
+
+
 @pytest.mark.parametrize("name", ["c2", "c4"])
 def test_rhs_full_size_sampled_cells(smc, name):
     """Full-size configurations, in the launch configuration the benchmark
-    uses, checked at sampled cells that the oracle evaluates one by one."""
+    uses, checked at sampled cells that the oracle evaluates one by one, in
+    extended precision (np.longdouble).
+
+    The bar is 1e-12 relative, or three times the FP64 conditioning floor of
+    the component where that floor is higher.  It is higher for one species
+    of c2: at h = L/64 its narrow-stencil diffusion term is ~4500 times
+    smaller than (rho D X)/h^2, so rounding X_k to FP64 alone moves the RHS
+    by ~3e-12 of the component's maximum (the FP64 oracle itself is 2.4e-12
+    off the extended-precision value there)."""
     wl = synth.workload(name, seed=1)
     g = wl.grid
     prim_g = synth.boxes_to_global(g, wl.prim)
@@ -146,11 +167,13 @@ def test_rhs_full_size_sampled_cells(smc, name):
     U = synth.global_to_boxes(g, U_g)
     F = synth.boxes_to_global(g, gpu_rhs(smc, wl, U))
     cells = _sample_cells(np.random.default_rng(0), g, 10)
-    ref = orhs.rhs_at(U_g, cells, wl.mech, g.dx)
-    got = np.stack([F[:, z, y, x] for z, y, x in cells], axis=1)
     full_scale = np.abs(F).reshape(F.shape[0], -1).max(axis=1)
+    ref, floor = conditioning_floor(U_g, cells, wl.mech, g.dx, full_scale)
+    got = np.stack([F[:, z, y, x] for z, y, x in cells], axis=1)
     err = np.abs(got - ref).max(axis=1) / full_scale
-    assert err.max() < TOL, err
+    bar = np.maximum(TOL, 3.0 * floor)
+    assert (err <= bar).all(), (err, floor)
+    assert (bar == TOL).sum() >= len(bar) - 1       # the floor decides at most one component
 
 
 def test_nan_input_reports_nonphysical(smc):
