@@ -42,7 +42,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="smc", choices=["smc", "reference"])
     ap.add_argument("--workload", default="c4")
-    ap.add_argument("--precision", default="fp64", choices=["fp64"])
+    ap.add_argument("--precision", default="both", choices=["fp64", "mixed", "both"],
+                    help="both: the mixed path is the headline, FP64 measured beside it")
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--n", type=int, default=None,
                     help="smaller instance of the workload (profiling captures)")
@@ -138,6 +139,38 @@ def march_flops_per_cell(ns: int, mode: int = 0) -> float:
     return 490 + 134 * ns + 4 + 2 * ns + 225 + 21 * ns + vc + 5 + ns
 
 
+def march_flops_per_cell_mixed(ns: int, mode: int = 0) -> float:
+    """FP32 flops of the mixed-precision stencil-direction kernel per cell,
+    counted from its source like march_flops_per_cell, with the float-pair
+    work: each pair difference costs 3 flops, each pair product 7."""
+    # faces: M u on pairs (44 fma + 7 pair diffs) = 109, M^T a = 81, pair dot
+    # (7 fma + 7 pair diffs) = 35, plain dot = 15
+    face = 109 + 2 * 81 + 3 * 35 + 3 * 35 + 2 + (109 + 15 + 1) + 16 + ns * (109 + 3 * 15 + 2)
+    diffs = 4 + 2 * ns
+    conv = 8 * (5 * 7 + 12) + 4 * (5 * 5 + 3 * 3) + 5 + ns * (4 * (2 * 7 + 3 + 2) + 1)
+    vc = (4 * 5 + 2) + ns * (4 * 5 + 2) + ns * (4 * 5 + 2) + (4 * 5 + 2) if mode == 0 else 0
+    return face + diffs + conv + vc + 5 + ns
+
+
+def chem_flops_per_eval(ns: int, nr: int, mol_sides: float = 4.0) -> float:
+    """FP64 flops of one production-rate evaluation per cell, counted from the
+    source (FMA = 2; the table-driven exponential = 20 flops, log = 20): per
+    reaction 43 (exponent 8, exponential 20, products and net rate ~7,
+    species updates 8), per species 49 (Gibbs energy 23, z_k with its
+    exponential 23, sums 3), 31 per cell (ln T, 1/T, pressure powers)."""
+    return 43.0 * nr + 49.0 * ns + 31.0
+
+
+def fine_flops_per_substep(ns: int, nr: int, M1: int, Y: int) -> float:
+    """One fine substep of the multirate chain per cell: the reaction
+    evaluation, the temperature Newton solve (mixture-polynomial setup
+    13 ns, ~5 iterations of 22) and the update of eq. mrupdate
+    (NV (2 + 2 (M1 + 1)) + ns (2 + 2 Y))."""
+    nv = 5 + ns
+    return (chem_flops_per_eval(ns, nr) + 13.0 * ns + 5 * 22 + 12
+            + nv * (2 + 2 * (M1 + 1)) + ns * (2 + 2 * Y))
+
+
 def measured_peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -198,7 +231,8 @@ def run_reference(args):
     line = {"impl": "reference", "metric": "Mcell-RHS/s (21 species)", "value": value,
             "unit": "Mcell-RHS/s", "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1000 * el / args.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64",
             "data": "synthetic", "config": {"workload": args.workload},
             "cpu_baseline": dict(last, value=value),
             "e2e": {"value": value, "unit": "Mcell-RHS/s", "h2d_bytes_per_step": 0,
@@ -228,69 +262,99 @@ def main():
     ncells = wl.grid.ncells
     nv = 5 + wl.mech.ns
 
-    h = smc.Smc(wl.grid, wl.mech)
-    stream = torch.cuda.Stream(device)
-    h.set_stream(stream)
-    prim = torch.from_numpy(wl.prim).to(device)
-    U = torch.empty_like(prim)
-    with torch.cuda.stream(stream):
-        h.prim_to_cons(prim, U)
-    h.synchronize()
-    del prim
-    U0 = U.clone()
+    def measure(precision: int):
+        """Warm up, then time args.steps steps on device-resident state."""
+        h = smc.Smc(wl.grid, wl.mech, {"precision": precision})
+        stream = torch.cuda.Stream(device)
+        h.set_stream(stream)
+        prim = torch.from_numpy(wl.prim).to(device)
+        U = torch.empty_like(prim)
+        with torch.cuda.stream(stream):
+            h.prim_to_cons(prim, U)
+        h.synchronize()
+        del prim
+        U0 = U.clone()
+        for _ in range(args.warmup):          # also fills the recycled f(U_0)
+            h.sdc_step(U, wl.dt, nodes, sweeps, rsub)
+        h.synchronize()
+        base = h.stats()
+        h.set_option("profile", 1)
+        sampler = ClockSampler(local)
+        barrier(world)
+        torch.cuda.synchronize(device)
+        sampler.start()
+        t_start = torch.cuda.Event(enable_timing=True)
+        t_end = torch.cuda.Event(enable_timing=True)
+        t_start.record(stream)
+        for _ in range(args.steps):
+            h.sdc_step(U, wl.dt, nodes, sweeps, rsub)
+        t_end.record(stream)
+        torch.cuda.synchronize(device)
+        clocks = sampler.stop()
+        barrier(world)
+        h.synchronize()
+        ms = max_over_ranks(world, t_start.elapsed_time(t_end), device)
+        st = h.stats()
+        h.set_option("profile", 0)
+        launches = {k: st["launches"][k] - base["launches"][k] for k in st["launches"]}
+        h.close()
+        return dict(ms_step=ms / args.steps, launches=launches, kms=st["kernel_ms"],
+                    clocks=clocks, U0=U0)
 
-    # warm-up (also fills the recycled f(U_0))
-    for _ in range(args.warmup):
-        h.sdc_step(U, wl.dt, nodes, sweeps, rsub)
-    h.synchronize()
-    base = h.stats()
-    h.set_option("profile", 1)
-    sampler = ClockSampler(local)
-    barrier(world)
-    torch.cuda.synchronize(device)
-    sampler.start()
-    t_start = torch.cuda.Event(enable_timing=True)
-    t_end = torch.cuda.Event(enable_timing=True)
-    t_start.record(stream)
-    for _ in range(args.steps):
-        h.sdc_step(U, wl.dt, nodes, sweeps, rsub)
-    t_end.record(stream)
-    torch.cuda.synchronize(device)
-    clocks = sampler.stop()
-    barrier(world)
-    h.synchronize()
-    ms = t_start.elapsed_time(t_end)
-    ms = max_over_ranks(world, ms, device)
-    st = h.stats()
-    h.set_option("profile", 0)
-    launches = {k: st["launches"][k] - base["launches"][k] for k in st["launches"]}
-    kms = st["kernel_ms"]
-    ms_step = ms / args.steps
+    runs = {}
+    if args.precision in ("mixed", "both"):
+        runs["mixed"] = measure(1)
+    if args.precision in ("fp64", "both"):
+        runs["fp64"] = measure(0)
+    main_key = "mixed" if "mixed" in runs else "fp64"
+    R = runs[main_key]
+    ms_step, launches, kms, clocks, U0 = R["ms_step"], R["launches"], R["kms"], R["clocks"], R["U0"]
     value = world * ncells * evals_per_step / (ms_step / 1e3) / 1e6
+    mixed_prec = 1 if main_key == "mixed" else 0
 
-    # dominant kernel: the stencil-direction kernel (FP64 pipe)
-    n_march = launches["march"]
-    march_ms = kms["march"] / max(n_march, 1)
-    flops_launch = march_flops_per_cell(wl.mech.ns) * ncells
+    # rooflines of the two heaviest kernels; "roofline" is the one with the
+    # larger share of the step
     sm_mhz = clocks.get("sm_mhz") or 2070.0
     fp64_peak = SM_COUNT * 4 * sm_mhz * 1e6          # 2 DFMA / clk / SM (1.25 TFLOP/s at 2.07 GHz)
-    achieved = flops_launch / (march_ms / 1e3)
+    fp32_peak = SM_COUNT * 256 * sm_mhz * 1e6        # 128 FP32 FMA / clk / SM
     prof = os.path.join(ROOT, "profiles", "traffic.json")
-    traffic = None
-    if os.path.exists(prof):
-        try:
-            traffic = json.load(open(prof)).get(f"k_march:{args.workload}")
-        except ValueError:
-            traffic = None
-    roofline = {"bound": "alu", "kernel": "k_march (one stencil direction)",
-                "achieved": achieved / 1e12, "peak": fp64_peak / 1e12, "unit": "TFLOP/s",
-                "frac": achieved / fp64_peak, "traffic": traffic,
-                "peak_source": "FP64 pipe: 152 SMs x 2 FMA/clk x median SM clock under load"}
+    try:
+        traffic_db = json.load(open(prof))
+    except (OSError, ValueError):
+        traffic_db = {}
+    rooflines = {}
+    n_march = launches["march"]
+    if n_march:
+        march_ms = kms["march"] / n_march
+        if main_key == "fp64":
+            fl, peak, src = march_flops_per_cell(wl.mech.ns) * ncells, fp64_peak, "FP64 pipe"
+        else:
+            fl, peak, src = march_flops_per_cell_mixed(wl.mech.ns) * ncells, fp32_peak, "FP32 pipe"
+        rooflines["k_march"] = {
+            "bound": "alu", "kernel": "k_march (one stencil direction)",
+            "achieved": fl / (march_ms / 1e3) / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s",
+            "frac": fl / (march_ms / 1e3) / peak,
+            "traffic": traffic_db.get(f"k_march:{main_key}:{args.workload}"),
+            "peak_source": f"{src}: 152 SMs x FMA/clk x median SM clock under load",
+            "share": kms["march"] / max(sum(kms.values()), 1e-9)}
+    n_fine = launches["fine"]
+    if n_fine:
+        per = rsub - 1
+        fine_ms = kms["fine"] / n_fine
+        fl = fine_flops_per_substep(wl.mech.ns, wl.mech.nr, M1, rsub) * ncells * per
+        rooflines["k_fine_chain"] = {
+            "bound": "alu", "kernel": "k_fine_chain (reaction substeps of one coarse interval)",
+            "achieved": fl / (fine_ms / 1e3) / 1e12, "peak": fp64_peak / 1e12, "unit": "TFLOP/s",
+            "frac": fl / (fine_ms / 1e3) / fp64_peak,
+            "traffic": traffic_db.get(f"k_fine_chain:{main_key}:{args.workload}"),
+            "peak_source": "FP64 pipe: 152 SMs x 2 FMA/clk x median SM clock under load",
+            "share": kms["fine"] / max(sum(kms.values()), 1e-9)}
+    roofline = max(rooflines.values(), key=lambda r: r["share"]) if rooflines else None
     # HBM-bound stage: SDC / fine-node updates
     peaks = measured_peaks()
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
-    # per fine-chain launch: U in + out, F1 (M1+3 arrays), F2 (fine group + 2) reads/writes
     per = rsub - 1 if rsub >= 2 else 0
+    M1 = nodes - 1
     if per:
         bytes_fine = ncells * 8 * (2 * nv + per * (M1 + 3) * nv + per * (rsub + 2) * wl.mech.ns)
         fine_ms = kms["fine"] / max(launches["fine"], 1)
@@ -299,10 +363,16 @@ def main():
                "note": "algorithmic bytes; the chain also evaluates reactions in FP64"}
     else:
         hbm = None
+    precision_report = {k: {"value": world * ncells * evals_per_step / (r["ms_step"] / 1e3) / 1e6,
+                            "ms_per_step": r["ms_step"],
+                            "kernel_ms_per_step": {kk: vv / args.steps for kk, vv in r["kms"].items()}}
+                        for k, r in runs.items()}
+    if "mixed" in runs and "fp64" in runs:
+        precision_report["mixed_speedup_vs_fp64"] = runs["fp64"]["ms_step"] / runs["mixed"]["ms_step"]
 
     # end to end: host buffers through the C ABI, copies inside the timed region
     Uh = U0.cpu().numpy().copy()
-    h2 = smc.Smc(wl.grid, wl.mech)
+    h2 = smc.Smc(wl.grid, wl.mech, {"precision": mixed_prec})
     h2.sdc_step(Uh, wl.dt, nodes, sweeps, rsub)
     e2e_steps = max(1, min(args.steps, 3))
     t0 = time.perf_counter()
@@ -319,7 +389,8 @@ def main():
         line = {
             "metric": "Mcell-RHS/s (21 species)", "value": value, "unit": "Mcell-RHS/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+f64" if main_key == "mixed" else "f64",
             "data": "synthetic",
             "config": {"workload": args.workload + (f" (n={args.n})" if args.n else ""), "boxes": wl.grid.nboxes, "cells": ncells,
                        "species": wl.mech.ns, "reactions": wl.mech.nr,
@@ -327,16 +398,17 @@ def main():
                                       if rsub >= 2 else f"SDC {nodes} GL, {sweeps} sweeps"),
                        "rhs_evals_per_step": evals_per_step,
                        "reaction_evals_per_step": sweeps * M1 * per if per else 0,
-                       "precision": args.precision,
+                       "precision": ("mixed: FP32 stencils/transport, FP64 T, Gibbs, exp, "
+                                     "rates, SDC accumulation") if main_key == "mixed" else "fp64",
                        "l2": "inputs larger than L2 (state %.0f MB)" % (nv * ncells * 8 / 1e6),
                        "parallelism": "replicas" if world > 1 else "single GPU"},
-            "roofline": roofline, "hbm": hbm, "cpu_baseline": cpu, "e2e": e2e,
+            "roofline": roofline, "rooflines": rooflines, "hbm": hbm, "cpu_baseline": cpu, "e2e": e2e,
+            "precisions": precision_report,
             "gpu_launches": int(sum(launches.values())),
             "kernel_ms_per_step": {k: kms[k] / args.steps for k in kms},
             "clocks": clocks,
         }
         print(json.dumps(line))
-    h.close()
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()

@@ -42,6 +42,7 @@ struct smc_handle {
   std::vector<double *> rpool;          // ns-component arrays
   double *d_U0 = nullptr;
   double *d_stage[3] = {nullptr, nullptr, nullptr};
+  float *d_dUf = nullptr;               // mixed precision: float stencil sums
 
   // recycled f(U_0) (Sec. 3.1): pool indices of the last step's end values
   const double *cache_U = nullptr;
@@ -289,6 +290,20 @@ smc_status ensure_pools(smc_handle *h, int nf, int nr) {
 smc_status eval_rhs(smc_handle *h, const double *U, double *F, int transport, int chemistry) {
   DevState s = state(h);
   const int chem = chemistry && h->opt.reactions && h->nr > 0;
+  if (h->precision == 1) {
+    if (!h->d_dUf) CUDA_TRY(h, dalloc(h, &h->d_dUf, (size_t)h->nv * h->ncells));
+    { Timed t(h, SMC_K_PRIM); launch_prim_m(s, U, h->stream); }
+    if (transport) {
+      { Timed t(h, SMC_K_GRAD); launch_grad_m(s, h->stream); }
+      for (int d = 0; d < 3; ++d) {
+        Timed t(h, SMC_K_MARCH);
+        launch_march_m(s, d, h->d_dUf, d == 0, h->stream);
+      }
+    }
+    { Timed t(h, SMC_K_FINAL); launch_final_m(s, U, h->d_dUf, F, transport, chem, h->stream); }
+    CUDA_TRY(h, cudaGetLastError());
+    return SMC_OK;
+  }
   { Timed t(h, SMC_K_PRIM); launch_prim(s, U, h->stream); }
   if (transport) {
     { Timed t(h, SMC_K_GRAD); launch_grad(s, h->stream); }
@@ -689,6 +704,7 @@ smc_status smc_destroy(smc_handle *h) {
   for (double *p : h->fpool) cudaFree(p);
   for (double *p : h->rpool) cudaFree(p);
   cudaFree(h->d_U0);
+  cudaFree(h->d_dUf);
   for (int i = 0; i < 3; ++i) cudaFree(h->d_stage[i]);
   for (auto &p : h->ev_pending) {
     h->ev_free.push_back(p.second.first);
@@ -792,7 +808,6 @@ smc_status smc_set_option(smc_handle *h, int key, double v) {
   switch (key) {
     case SMC_OPT_PRECISION:
       if (v != 0.0 && v != 1.0) return fail(h, SMC_ERR_ARG, "precision must be 0 or 1");
-      if (v == 1.0) return fail(h, SMC_ERR_ARG, "mixed precision is not available in this build");
       h->precision = (int)v;
       return SMC_OK;
     case SMC_OPT_M47: h->m47 = v; build_coef(h); return SMC_OK;

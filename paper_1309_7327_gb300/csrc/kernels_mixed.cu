@@ -1,0 +1,503 @@
+// Mixed-precision right-hand side: stencil, transport and correction-velocity
+// arithmetic in FP32; temperature inversion, Gibbs energies, exponentials,
+// production rates and the result accumulation in FP64.
+//
+// Fields that enter differences (velocities, T, p, kinetic energies, h, rho,
+// rho H, Y_k, X_k, rho Y_k) are stored as float pairs hi + lo with
+// hi = fl32(x), lo = fl32(x - hi) (about 48 significant bits); a difference
+// x_a - x_b is formed as (hi_a - hi_b) + (lo_a - lo_b), accurate to FP32
+// rounding of the difference itself rather than of x.  Coefficients (eta,
+// lambda, rho D_k, B_k, ...) are plain floats.  Products that form
+// convective fluxes (rho u_d, rho u_c u_d, rho H u_d, rho Y_k u_d) are
+// carried as float pairs through an FMA-based exact product.
+#include "chem.cuh"
+#include "smc_internal.h"
+
+namespace smc {
+
+// float-plane indices of the mixed-precision scratch (reuses the FP64 Q buffer)
+enum {
+  PM_U = 0, PM_V = 2, PM_W = 4, PM_T = 6, PM_P = 8, PM_KX = 10, PM_KY = 12, PM_KZ = 14,
+  PM_HMIX = 16, PM_RHO = 18, PM_RHOH = 20,
+  PM_C43 = 22, PM_ETA, PM_C23, PM_LAM, PM_AP, PM_SB, PM_NBASE
+};
+__host__ __device__ inline int pmY(int ns, int k) { return PM_NBASE + 2 * k; }
+__host__ __device__ inline int pmX(int ns, int k) { return PM_NBASE + 2 * ns + 2 * k; }
+__host__ __device__ inline int pmRY(int ns, int k) { return PM_NBASE + 4 * ns + 2 * k; }
+__host__ __device__ inline int pmRD(int ns, int k) { return PM_NBASE + 6 * ns + k; }
+__host__ __device__ inline int pmRDH(int ns, int k) { return PM_NBASE + 7 * ns + k; }
+__host__ __device__ inline int pmB(int ns, int k) { return PM_NBASE + 8 * ns + k; }
+int nQm(int ns) { return PM_NBASE + 9 * ns; }
+
+struct f2 {
+  float h, l;
+};
+
+__device__ __forceinline__ void put_pair(float *Qf, size_t NG, int plane, long long g, double x) {
+  const float h = __double2float_rn(x);
+  Qf[(size_t)plane * NG + g] = h;
+  Qf[(size_t)(plane + 1) * NG + g] = __double2float_rn(x - (double)h);
+}
+
+__device__ __forceinline__ f2 get_pair(const float *__restrict__ Qf, size_t NG, int plane,
+                                       long long g) {
+  f2 r;
+  r.h = __ldg(Qf + (size_t)plane * NG + g);
+  r.l = __ldg(Qf + (size_t)(plane + 1) * NG + g);
+  return r;
+}
+
+__device__ __forceinline__ float diff(f2 a, f2 b) { return (a.h - b.h) + (a.l - b.l); }
+
+// a * b as a float pair (exact product of the high parts plus the cross terms)
+__device__ __forceinline__ f2 mul(f2 a, f2 b) {
+  f2 r;
+  r.h = a.h * b.h;
+  r.l = fmaf(a.h, b.h, -r.h) + fmaf(a.h, b.l, a.l * b.h);
+  return r;
+}
+
+__device__ __forceinline__ f2 mulf(f2 a, float b) {
+  f2 r;
+  r.h = a.h * b;
+  r.l = fmaf(a.h, b, -r.h) + a.l * b;
+  return r;
+}
+
+// ------------------------------------------------------------ k_prim_m
+__global__ void __launch_bounds__(128) k_prim_m(const DevState s, const double *__restrict__ U) {
+  const Mech &m = *s.mech;
+  const int ns = s.ns;
+  const long long NG = s.nghost, NI = s.ncells;
+  float *__restrict__ Qf = reinterpret_cast<float *>(s.Q);
+  const int mode = s.opt.mode, ref = s.opt.ref;
+  for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < NG;
+       g += (long long)gridDim.x * blockDim.x) {
+    const long long src = s.gmap[g];
+    const double rho = U[src];
+    const double invrho = 1.0 / rho;
+    const double u = U[NI + src] * invrho;
+    const double v = U[2 * NI + src] * invrho;
+    const double w = U[3 * NI + src] * invrho;
+    const double rhoE = U[4 * NI + src];
+    double Y[SMC_MAX_NS];
+    for (int k = 0; k < ns; ++k) Y[k] = U[(5 + k) * NI + src] * invrho;
+    const double e = rhoE * invrho - 0.5 * (u * u + v * v + w * w);
+    double T;
+    const bool ok = newton_T(m, Y, e, s.opt.T0, s.opt.tol, s.opt.maxit, T);
+    unsigned flag = 0;
+    if (!ok) flag |= ST_NONCONV;
+    if (!(rho > 0.0) || !(T > 0.0)) flag |= ST_NONPHYS;
+    if (!isfinite(rho) || !isfinite(rhoE) || !isfinite(T)) flag |= ST_NONFINITE;
+    if (flag) atomicOr(s.status, flag);
+
+    double wmix = 0.0, hm = 0.0;
+    float cpm = 0.0f;
+    const float Tf = (float)T;
+    float h32[SMC_MAX_NS];
+    for (int k = 0; k < ns; ++k) {
+      wmix += Y[k] * m.invW[k];
+      const double hk = m.Ru_W[k] * hR(m, k, T);
+      hm += Y[k] * hk;
+      h32[k] = (float)hk;
+      const float cp = (float)m.cp[k][0] + Tf * ((float)m.cp[k][1] + Tf * ((float)m.cp[k][2] +
+                       Tf * ((float)m.cp[k][3] + Tf * (float)m.cp[k][4])));
+      cpm += (float)Y[k] * (float)m.Ru_W[k] * cp;
+    }
+    const double p = rho * kRu * T * wmix;
+    const float invp = 1.0f / (float)p;
+    const double inv_wmix = 1.0 / wmix;
+    // transport in FP32
+    const float eta = (float)m.eta_ref * __powf(Tf * (float)m.inv_T_ref, (float)m.eta_exp);
+    const float xi = (float)s.opt.xi_ratio * eta;
+    const float lam = cpm * eta * (float)m.inv_Pr;
+    const float rd0 = lam / cpm;
+    put_pair(Qf, NG, PM_U, g, u);
+    put_pair(Qf, NG, PM_V, g, v);
+    put_pair(Qf, NG, PM_W, g, w);
+    put_pair(Qf, NG, PM_T, g, T);
+    put_pair(Qf, NG, PM_P, g, p);
+    put_pair(Qf, NG, PM_KX, g, 0.5 * u * u);
+    put_pair(Qf, NG, PM_KY, g, 0.5 * v * v);
+    put_pair(Qf, NG, PM_KZ, g, 0.5 * w * w);
+    put_pair(Qf, NG, PM_HMIX, g, hm);
+    put_pair(Qf, NG, PM_RHO, g, rho);
+    put_pair(Qf, NG, PM_RHOH, g, rhoE + p);
+    Qf[(size_t)PM_C43 * NG + g] = 4.0f / 3.0f * eta + xi;
+    Qf[(size_t)PM_ETA * NG + g] = eta;
+    Qf[(size_t)PM_C23 * NG + g] = xi - 2.0f / 3.0f * eta;
+    Qf[(size_t)PM_LAM * NG + g] = lam;
+    const float href = (mode == 1) ? h32[ref] : 0.0f;
+    float ap = 0.0f, sb = 0.0f;
+    for (int k = 0; k < ns; ++k) {
+      const double X = Y[k] * m.invW[k] * inv_wmix;
+      const float rd = rd0 * (float)m.invLe[k];
+      const float B = rd * (float)(X - Y[k]) * invp;
+      const float hp = h32[k] - href;
+      if (mode == 0) {
+        ap += h32[k] * B;
+        sb += B;
+      } else if (k != ref) {
+        ap += hp * B;
+      }
+      put_pair(Qf, NG, pmY(ns, k), g, Y[k]);
+      put_pair(Qf, NG, pmX(ns, k), g, X);
+      put_pair(Qf, NG, pmRY(ns, k), g, U[(5 + k) * NI + src]);
+      Qf[(size_t)pmRD(ns, k) * NG + g] = rd;
+      Qf[(size_t)pmRDH(ns, k) * NG + g] = rd * hp;
+      Qf[(size_t)pmB(ns, k) * NG + g] = B;
+    }
+    Qf[(size_t)PM_AP * NG + g] = ap;
+    Qf[(size_t)PM_SB * NG + g] = sb;
+  }
+}
+
+// ------------------------------------------------------------ k_grad_m
+struct GradParamsM {
+  float D[3][4];
+};
+
+__device__ __forceinline__ int find_box_m(const Box *__restrict__ b, int nb, long long g) {
+  int lo = 0, hi = nb - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (b[mid].off_g <= g) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+__global__ void __launch_bounds__(128) k_grad_m(const DevState s, const GradParamsM P) {
+  const long long NG = s.nghost;
+  const float *__restrict__ Qf = reinterpret_cast<const float *>(s.Q);
+  float *__restrict__ Gf = reinterpret_cast<float *>(s.G);
+  for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < NG;
+       g += (long long)gridDim.x * blockDim.x) {
+    const Box B = s.boxes[find_box_m(s.boxes, s.nboxes, g)];
+    const long long l = g - B.off_g;
+    const int crd[3] = {(int)(l % B.gx) - SMC_GHOST, (int)((l / B.gx) % B.gy) - SMC_GHOST,
+                        (int)(l / ((long long)B.gx * B.gy)) - SMC_GHOST};
+    const int n[3] = {B.nx, B.ny, B.nz};
+    const long long stride[3] = {1, B.gx, (long long)B.gx * B.gy};
+    int ng = 0;
+    for (int e = 0; e < 3; ++e) ng += (crd[e] < 0 || crd[e] >= n[e]);
+    for (int e = 0; e < 3; ++e) {
+      if (crd[e] < 0 || crd[e] >= n[e] || ng > 1) continue;
+      for (int c = 0; c < 3; ++c) {
+        float acc = 0.0f;
+#pragma unroll
+        for (int k = 1; k <= 4; ++k)
+          acc += P.D[e][k - 1] * diff(get_pair(Qf, NG, PM_U + 2 * c, g + k * stride[e]),
+                                      get_pair(Qf, NG, PM_U + 2 * c, g - k * stride[e]));
+        Gf[(size_t)(3 * e + c) * NG + g] = acc;
+      }
+    }
+  }
+}
+
+// ------------------------------------------------------------ k_march_m
+struct MarchParamsM {
+  float M[8][8];
+  float D[4];
+};
+
+// w[m] = sum_{n != 3} M[m][n] (x_n - x_3) for a window of float pairs
+__device__ __forceinline__ void mv_pair(const MarchParamsM &P, const float *__restrict__ Qf,
+                                        size_t NG, int plane, long long gw, int sg, float *w) {
+  float d[8];
+  const f2 x3 = get_pair(Qf, NG, plane, gw + 3 * sg);
+#pragma unroll
+  for (int t = 0; t < 8; ++t) d[t] = (t == 3) ? 0.0f : diff(get_pair(Qf, NG, plane, gw + t * sg), x3);
+#pragma unroll
+  for (int mm = 0; mm < 8; ++mm) {
+    float acc = 0.0f;
+#pragma unroll
+    for (int t = 0; t < 8; ++t)
+      if (t != 3 && mm - t <= 4 && t - mm <= 4) acc = fmaf(P.M[mm][t], d[t], acc);
+    w[mm] = acc;
+  }
+}
+
+// v[n] = sum_m a_m M[m][n] (n != 3) for a window of floats
+__device__ __forceinline__ void vm_single(const MarchParamsM &P, const float *__restrict__ Qf,
+                                          size_t NG, int plane, long long gw, int sg, float *v) {
+  float a[8];
+#pragma unroll
+  for (int t = 0; t < 8; ++t) a[t] = __ldg(Qf + (size_t)plane * NG + gw + t * sg);
+#pragma unroll
+  for (int n = 0; n < 8; ++n) {
+    float acc = 0.0f;
+#pragma unroll
+    for (int mm = 0; mm < 8; ++mm)
+      if (n != 3 && mm - n <= 4 && n - mm <= 4) acc = fmaf(a[mm], P.M[mm][n], acc);
+    v[n] = acc;
+  }
+}
+
+// sum_{n != 3} v_n (x_n - x_3) for a window of float pairs
+__device__ __forceinline__ float dot_pair(const float *v, const float *__restrict__ Qf, size_t NG,
+                                          int plane, long long gw, int sg) {
+  const f2 x3 = get_pair(Qf, NG, plane, gw + 3 * sg);
+  float acc = 0.0f;
+#pragma unroll
+  for (int t = 0; t < 8; ++t)
+    if (t != 3) acc = fmaf(v[t], diff(get_pair(Qf, NG, plane, gw + t * sg), x3), acc);
+  return acc;
+}
+
+// sum_m a_m w_m for a window of floats
+__device__ __forceinline__ float dot_single(const float *w, const float *__restrict__ Qf, size_t NG,
+                                            int plane, long long gw, int sg) {
+  float acc = 0.0f;
+#pragma unroll
+  for (int t = 0; t < 8; ++t) acc = fmaf(__ldg(Qf + (size_t)plane * NG + gw + t * sg), w[t], acc);
+  return acc;
+}
+
+template <int DIR>
+__device__ __forceinline__ void face_fluxes_m(const DevState &s, const MarchParamsM &P, long long gw,
+                                              int sg, float *H) {
+  constexpr int E = (DIR + 1) % 3, F = (DIR + 2) % 3;
+  const size_t NG = (size_t)s.nghost;
+  const float *__restrict__ Qf = reinterpret_cast<const float *>(s.Q);
+  const int ns = s.ns, mode = s.opt.mode, ref = s.opt.ref;
+  float wp[8], vA[8], vB[8], wk[8];
+  mv_pair(P, Qf, NG, PM_P, gw, sg, wp);
+  vm_single(P, Qf, NG, PM_C43, gw, sg, vA);
+  vm_single(P, Qf, NG, PM_ETA, gw, sg, vB);
+  H[0] = dot_pair(vA, Qf, NG, PM_U + 2 * DIR, gw, sg);
+  H[1] = dot_pair(vB, Qf, NG, PM_U + 2 * E, gw, sg);
+  H[2] = dot_pair(vB, Qf, NG, PM_U + 2 * F, gw, sg);
+  float HE = dot_pair(vA, Qf, NG, PM_KX + 2 * DIR, gw, sg);
+  HE += dot_pair(vB, Qf, NG, PM_KX + 2 * E, gw, sg);
+  HE += dot_pair(vB, Qf, NG, PM_KX + 2 * F, gw, sg);
+  mv_pair(P, Qf, NG, PM_T, gw, sg, wk);
+  HE += dot_single(wk, Qf, NG, PM_LAM, gw, sg);
+  HE += dot_single(wp, Qf, NG, PM_AP, gw, sg);
+  for (int k = 0; k < ns; ++k) {
+    if (mode == 1 && k == ref) {
+      H[4 + k] = 0.0f;
+      continue;
+    }
+    mv_pair(P, Qf, NG, pmX(ns, k), gw, sg, wk);
+    H[4 + k] = dot_single(wk, Qf, NG, pmRD(ns, k), gw, sg) + dot_single(wp, Qf, NG, pmB(ns, k), gw, sg);
+    HE += dot_single(wk, Qf, NG, pmRDH(ns, k), gw, sg);
+  }
+  H[3] = HE;
+}
+
+template <int DIR>
+__global__ void __launch_bounds__(128, 4) k_march_m(const DevState s, const MarchParamsM P,
+                                                    float *__restrict__ dUf, int first) {
+  const long long item = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (item >= s.nlines[DIR]) return;
+  const LineItem L = s.lines[DIR][item];
+  constexpr int E = (DIR + 1) % 3, F = (DIR + 2) % 3;
+  const int ns = s.ns, nv = s.nv, mode = s.opt.mode, ref = s.opt.ref;
+  const size_t NG = (size_t)s.nghost, NI = (size_t)s.ncells;
+  const float *__restrict__ Qf = reinterpret_cast<const float *>(s.Q);
+  const float *__restrict__ Gf = reinterpret_cast<const float *>(s.G);
+  float *__restrict__ divf = reinterpret_cast<float *>(s.divacc);
+  const int sg = L.sg;
+
+  float Hp[4 + SMC_MAX_NS], Hn[4 + SMC_MAX_NS], out[5 + SMC_MAX_NS];
+  face_fluxes_m<DIR>(s, P, L.g0 - 4LL * sg, sg, Hp);
+  for (int c = 0; c < L.len; ++c) {
+    const long long gc = L.g0 + (long long)c * sg;
+    const long long ic = L.i0 + (long long)c * L.si;
+    face_fluxes_m<DIR>(s, P, gc - 3LL * sg, sg, Hn);
+    out[0] = 0.0f;
+    out[1 + DIR] = Hn[0] - Hp[0];
+    out[1 + E] = Hn[1] - Hp[1];
+    out[1 + F] = Hn[2] - Hp[2];
+    out[4] = Hn[3] - Hp[3];
+    float sumN = 0.0f;
+    for (int k = 0; k < ns; ++k) {
+      const float N = Hn[4 + k] - Hp[4 + k];
+      out[5 + k] = N;
+      sumN += N;
+    }
+    if (mode == 1) out[5 + ref] = -sumN;
+
+    // -D_d of the convective fluxes (float-pair products) and mixed viscous terms
+    float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f, a4 = 0.f;
+    f2 udp[4], udm[4];
+#pragma unroll
+    for (int n = 1; n <= 4; ++n) {
+      f2 fl[2][5];
+      float vis[2][3];
+#pragma unroll
+      for (int side = 0; side < 2; ++side) {
+        const long long j = side == 0 ? gc + n * sg : gc - n * sg;
+        const f2 rho = get_pair(Qf, NG, PM_RHO, j), ud = get_pair(Qf, NG, PM_U + 2 * DIR, j);
+        const f2 ue = get_pair(Qf, NG, PM_U + 2 * E, j), uf = get_pair(Qf, NG, PM_U + 2 * F, j);
+        const f2 rH = get_pair(Qf, NG, PM_RHOH, j);
+        const float c23 = __ldg(Qf + (size_t)PM_C23 * NG + j), eta = __ldg(Qf + (size_t)PM_ETA * NG + j);
+        const float Gee = __ldg(Gf + (size_t)(3 * E + E) * NG + j);
+        const float Gff = __ldg(Gf + (size_t)(3 * F + F) * NG + j);
+        const float Ged = __ldg(Gf + (size_t)(3 * E + DIR) * NG + j);
+        const float Gfd = __ldg(Gf + (size_t)(3 * F + DIR) * NG + j);
+        const float tdiv = c23 * (Gee + Gff);
+        const f2 mass = mul(rho, ud);
+        fl[side][0] = mass;
+        fl[side][1] = mul(mass, ud);
+        fl[side][2] = mul(mass, ue);
+        fl[side][3] = mul(mass, uf);
+        fl[side][4] = mul(rH, ud);
+        vis[side][0] = tdiv;
+        vis[side][1] = eta * Ged;
+        vis[side][2] = eta * Gfd;
+        // viscous work: tdiv u_d + eta (Ged u_e + Gfd u_f), plain floats
+        fl[side][4].l -= tdiv * (ud.h + ud.l) + eta * (Ged * (ue.h + ue.l) + Gfd * (uf.h + uf.l));
+        if (side == 0) udp[n - 1] = ud; else udm[n - 1] = ud;
+      }
+      const float dn = P.D[n - 1];
+      const f2 pp = get_pair(Qf, NG, PM_P, gc + n * sg), pm = get_pair(Qf, NG, PM_P, gc - n * sg);
+      a0 = fmaf(dn, diff(fl[0][0], fl[1][0]), a0);
+      a1 = fmaf(dn, diff(fl[0][1], fl[1][1]) + diff(pp, pm) - (vis[0][0] - vis[1][0]), a1);
+      a2 = fmaf(dn, diff(fl[0][2], fl[1][2]) - (vis[0][1] - vis[1][1]), a2);
+      a3 = fmaf(dn, diff(fl[0][3], fl[1][3]) - (vis[0][2] - vis[1][2]), a3);
+      a4 = fmaf(dn, diff(fl[0][4], fl[1][4]), a4);
+    }
+    out[0] -= a0;
+    out[1 + DIR] -= a1;
+    out[1 + E] -= a2;
+    out[1 + F] -= a3;
+    out[4] -= a4;
+    for (int k = 0; k < ns; ++k) {
+      float acc = 0.0f;
+#pragma unroll
+      for (int n = 1; n <= 4; ++n)
+        acc = fmaf(P.D[n - 1], diff(mul(get_pair(Qf, NG, pmRY(ns, k), gc + n * sg), udp[n - 1]),
+                                    mul(get_pair(Qf, NG, pmRY(ns, k), gc - n * sg), udm[n - 1])), acc);
+      out[5 + k] -= acc;
+    }
+
+    if (mode == 0) {
+      float Dp = 0.0f;
+#pragma unroll
+      for (int n = 1; n <= 4; ++n)
+        Dp = fmaf(P.D[n - 1], diff(get_pair(Qf, NG, PM_P, gc + n * sg), get_pair(Qf, NG, PM_P, gc - n * sg)), Dp);
+      float Vc = -__ldg(Qf + (size_t)PM_SB * NG + gc) * Dp;
+      for (int l = 0; l < ns; ++l) {
+        float DX = 0.0f;
+#pragma unroll
+        for (int n = 1; n <= 4; ++n)
+          DX = fmaf(P.D[n - 1], diff(get_pair(Qf, NG, pmX(ns, l), gc + n * sg),
+                                     get_pair(Qf, NG, pmX(ns, l), gc - n * sg)), DX);
+        Vc -= __ldg(Qf + (size_t)pmRD(ns, l) * NG + gc) * DX;
+      }
+      for (int k = 0; k < ns; ++k) {
+        float DY = 0.0f;
+#pragma unroll
+        for (int n = 1; n <= 4; ++n)
+          DY = fmaf(P.D[n - 1], diff(get_pair(Qf, NG, pmY(ns, k), gc + n * sg),
+                                     get_pair(Qf, NG, pmY(ns, k), gc - n * sg)), DY);
+        out[5 + k] += DY * Vc;
+      }
+      float Dh = 0.0f;
+#pragma unroll
+      for (int n = 1; n <= 4; ++n)
+        Dh = fmaf(P.D[n - 1], diff(get_pair(Qf, NG, PM_HMIX, gc + n * sg),
+                                   get_pair(Qf, NG, PM_HMIX, gc - n * sg)), Dh);
+      out[4] += Dh * Vc;
+      if (first) divf[ic] = sumN; else divf[ic] += sumN;
+    }
+    if (first) {
+      for (int c2 = 0; c2 < nv; ++c2) dUf[(size_t)c2 * NI + ic] = out[c2];
+    } else {
+      for (int c2 = 0; c2 < nv; ++c2) dUf[(size_t)c2 * NI + ic] += out[c2];
+    }
+    for (int x = 0; x < 4 + ns; ++x) Hp[x] = Hn[x];
+  }
+}
+
+// ------------------------------------------------------------ k_final_m
+// dUdt (FP64) = float stencil sum + correction terms (FP32) + rho omega_k (FP64)
+__global__ void __launch_bounds__(128) k_final_m(const DevState s, const double *__restrict__ U,
+                                                 const float *__restrict__ dUf,
+                                                 double *__restrict__ dU, int transport,
+                                                 int chemistry) {
+  const Mech &m = *s.mech;
+  const int ns = s.ns, nv = s.nv;
+  const size_t NG = (size_t)s.nghost, NI = (size_t)s.ncells;
+  const float *__restrict__ Qf = reinterpret_cast<const float *>(s.Q);
+  const float *__restrict__ divf = reinterpret_cast<const float *>(s.divacc);
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < (long long)NI;
+       i += (long long)gridDim.x * blockDim.x) {
+    const long long g = s.imap[i];
+    double add[SMC_MAX_NS];
+    for (int k = 0; k < ns; ++k) add[k] = 0.0;
+    if (chemistry) {
+      // temperature from the conserved state, then the FP64 rates
+      double Uc[5 + SMC_MAX_NS], wd[SMC_MAX_NS], Y[SMC_MAX_NS];
+      for (int c = 0; c < nv; ++c) Uc[c] = U[(size_t)c * NI + i];
+      const double invrho = 1.0 / Uc[0];
+      for (int k = 0; k < ns; ++k) Y[k] = Uc[5 + k] * invrho;
+      const f2 Tp = get_pair(Qf, NG, PM_T, g);
+      const double T = (double)Tp.h + (double)Tp.l;
+      production_rates(m, s.rx, Uc[0], T, Y, wd);
+      for (int k = 0; k < ns; ++k) add[k] = wd[k];
+    }
+    if (transport) {
+      float corr[SMC_MAX_NS];
+      float corrE = 0.0f;
+      for (int k = 0; k < ns; ++k) corr[k] = 0.0f;
+      if (s.opt.mode == 0) {
+        const float divVc = -divf[i];
+        const f2 hm = get_pair(Qf, NG, PM_HMIX, g);
+        corrE = (hm.h + hm.l) * divVc;
+        for (int k = 0; k < ns; ++k) {
+          const f2 y = get_pair(Qf, NG, pmY(ns, k), g);
+          corr[k] = (y.h + y.l) * divVc;
+        }
+      }
+      for (int c = 0; c < 4; ++c) dU[(size_t)c * NI + i] = (double)dUf[(size_t)c * NI + i];
+      dU[4 * NI + i] = (double)(dUf[4 * NI + i] + corrE);
+      for (int k = 0; k < ns; ++k)
+        dU[(5 + k) * NI + i] = (double)(dUf[(5 + k) * NI + i] + corr[k]) + add[k];
+    } else {
+      for (int c = 0; c < 5; ++c) dU[(size_t)c * NI + i] = 0.0;
+      for (int k = 0; k < ns; ++k) dU[(5 + k) * NI + i] = add[k];
+    }
+  }
+}
+
+// ------------------------------------------------------------ launchers
+static int grid_for(long long n, int block) {
+  long long b = (n + block - 1) / block;
+  const long long cap = 152LL * 64;
+  if (b > cap) b = cap;
+  if (b < 1) b = 1;
+  return (int)b;
+}
+
+void launch_prim_m(const DevState &s, const double *U, cudaStream_t st) {
+  k_prim_m<<<grid_for(s.nghost, 128), 128, 0, st>>>(s, U);
+}
+
+void launch_grad_m(const DevState &s, cudaStream_t st) {
+  GradParamsM P;
+  for (int d = 0; d < 3; ++d)
+    for (int k = 0; k < 4; ++k) P.D[d][k] = (float)s.hcoef->D[d][k];
+  k_grad_m<<<grid_for(s.nghost, 128), 128, 0, st>>>(s, P);
+}
+
+void launch_march_m(const DevState &s, int dir, float *dUf, int first, cudaStream_t st) {
+  MarchParamsM P;
+  for (int a = 0; a < 8; ++a)
+    for (int b = 0; b < 8; ++b) P.M[a][b] = (float)s.hcoef->M[dir][a][b];
+  for (int k = 0; k < 4; ++k) P.D[k] = (float)s.hcoef->D[dir][k];
+  const long long n = s.nlines[dir];
+  if (n == 0) return;
+  const int blocks = (int)((n + 127) / 128);
+  if (dir == 0) k_march_m<0><<<blocks, 128, 0, st>>>(s, P, dUf, first);
+  else if (dir == 1) k_march_m<1><<<blocks, 128, 0, st>>>(s, P, dUf, first);
+  else k_march_m<2><<<blocks, 128, 0, st>>>(s, P, dUf, first);
+}
+
+void launch_final_m(const DevState &s, const double *U, const float *dUf, double *dU, int transport,
+                    int chemistry, cudaStream_t st) {
+  k_final_m<<<grid_for(s.ncells, 128), 128, 0, st>>>(s, U, dUf, dU, transport, chemistry);
+}
+
+}  // namespace smc

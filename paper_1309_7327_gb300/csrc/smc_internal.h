@@ -122,6 +122,15 @@ void launch_march(const DevState &s, int dir, double *dUdt, int first, cudaStrea
 void launch_final(const DevState &s, double *dUdt, int transport, int chemistry, cudaStream_t st);
 void launch_prim_to_cons(const DevState &s, const double *prim, double *U, cudaStream_t st);
 
+// Mixed precision (kernels_mixed.cu): FP32 stencils / transport on float-pair
+// scratch in the Q buffer, FP64 temperature, chemistry and accumulation.
+int nQm(int ns);
+void launch_prim_m(const DevState &s, const double *U, cudaStream_t st);
+void launch_grad_m(const DevState &s, cudaStream_t st);
+void launch_march_m(const DevState &s, int dir, float *dUf, int first, cudaStream_t st);
+void launch_final_m(const DevState &s, const double *U, const float *dUf, double *dU, int transport,
+                    int chemistry, cudaStream_t st);
+
 // out = in + sum_i c[i] * src[i] over n doubles (n = nv * ncells)
 struct Combo {
   int nsrc;
