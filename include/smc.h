@@ -130,7 +130,7 @@ enum {
   SMC_K_UPDATE = 4,     /* SDC node update */
   SMC_K_FINE = 5,       /* multirate fine-node reaction chain */
   SMC_K_CHEM = 6,       /* reaction-only evaluation */
-  SMC_K_OTHER = 7,      /* primitive-to-conserved conversion */
+  SMC_K_OTHER = 7,      /* primitive-to-conserved conversion, layout copies */
   SMC_NKERNELS = 8
 };
 

@@ -34,6 +34,8 @@ struct smc_handle {
   long long *d_imap = nullptr;
   LineItem *d_lines[3] = {nullptr, nullptr, nullptr};
   long long nlines[3] = {0, 0, 0};
+  LineItem *d_lines_xt = nullptr;       // x lines in the x-slowest (transposed) layout
+  double *d_Qt = nullptr, *d_Gt = nullptr;
   double *d_Q = nullptr, *d_G = nullptr, *d_divacc = nullptr;
   unsigned *d_status = nullptr;
 
@@ -145,9 +147,12 @@ DevState state(smc_handle *h) {
   }
   s.Q = h->d_Q;
   s.G = h->d_G;
+  s.Qt = h->d_Qt;
+  s.Gt = h->d_Gt;
   s.divacc = h->d_divacc;
   s.status = h->d_status;
   s.opt = h->opt;
+  s.xi_ratio_f = (float)h->opt.xi_ratio;
   return s;
 }
 
@@ -241,6 +246,31 @@ smc_status build_lines(smc_handle *h) {
     CUDA_TRY(h, dalloc(h, &h->d_lines[d], items.size()));
     CUDA_TRY(h, cudaMemcpy(h->d_lines[d], items.data(), items.size() * sizeof(LineItem),
                            cudaMemcpyHostToDevice));
+    if (d == 0) {
+      // the same x segments addressed in the [x][z][y] copy of each box
+      std::vector<LineItem> xt = items;
+      size_t t = 0;
+      for (int b = 0; b < h->nboxes; ++b) {
+        const Box &B = h->boxes[b];
+        int nseg = (B.nx + h->segment - 1) / h->segment;
+        if (nseg < 1) nseg = 1;
+        for (int sgi = 0; sgi < nseg; ++sgi) {
+          const int s0 = (int)((long long)B.nx * sgi / nseg);
+          for (int z = 0; z < B.nz; ++z)
+            for (int y = 0; y < B.ny; ++y) {
+              xt[t].g0 = B.off_g + ((long long)(s0 + SMC_GHOST) * B.gz + (z + SMC_GHOST)) * B.gy +
+                         (y + SMC_GHOST);
+              xt[t].sg = B.gy * B.gz;
+              ++t;
+            }
+        }
+      }
+      if (h->d_lines_xt) cudaFree(h->d_lines_xt);
+      h->d_lines_xt = nullptr;
+      CUDA_TRY(h, dalloc(h, &h->d_lines_xt, xt.size()));
+      CUDA_TRY(h, cudaMemcpy(h->d_lines_xt, xt.data(), xt.size() * sizeof(LineItem),
+                             cudaMemcpyHostToDevice));
+    }
   }
   return SMC_OK;
 }
@@ -292,12 +322,30 @@ smc_status eval_rhs(smc_handle *h, const double *U, double *F, int transport, in
   const int chem = chemistry && h->opt.reactions && h->nr > 0;
   if (h->precision == 1) {
     if (!h->d_dUf) CUDA_TRY(h, dalloc(h, &h->d_dUf, (size_t)h->nv * h->ncells));
+    if (!h->d_Qt) {
+      // float planes: the x-slowest copy of Q and of the gradients
+      CUDA_TRY(h, dalloc(h, reinterpret_cast<float **>(&h->d_Qt), (size_t)nQm(h->ns) * h->nghost));
+      CUDA_TRY(h, dalloc(h, reinterpret_cast<float **>(&h->d_Gt), (size_t)9 * h->nghost));
+      s = state(h);
+    }
     { Timed t(h, SMC_K_PRIM); launch_prim_m(s, U, h->stream); }
     if (transport) {
       { Timed t(h, SMC_K_GRAD); launch_grad_m(s, h->stream); }
+      {
+        // x lines read a copy with x the slowest index, so that consecutive
+        // threads (consecutive y) read consecutive addresses
+        { Timed t(h, SMC_K_OTHER); launch_transpose_x(s, s.Q, s.Qt, nQm(h->ns), 4, h->stream); }
+        Timed t(h, SMC_K_OTHER);
+        launch_transpose_x(s, reinterpret_cast<float *>(s.G) + 3 * (size_t)h->nghost,
+                           reinterpret_cast<float *>(s.Gt) + 3 * (size_t)h->nghost, 6, 4, h->stream);
+      }
+      DevState sx = s;
+      sx.Q = s.Qt;
+      sx.G = s.Gt;
+      sx.lines[0] = h->d_lines_xt;
       for (int d = 0; d < 3; ++d) {
         Timed t(h, SMC_K_MARCH);
-        launch_march_m(s, d, h->d_dUf, d == 0, h->stream);
+        launch_march_m(d == 0 ? sx : s, d, h->d_dUf, d == 0, h->stream);
       }
     }
     { Timed t(h, SMC_K_FINAL); launch_final_m(s, U, h->d_dUf, F, transport, chem, h->stream); }
@@ -515,6 +563,10 @@ smc_status smc_create(const smc_grid *grid, const smc_mechanism *mech, const smc
     M.sR[k][3] = a[2] / 2;
     M.sR[k][4] = a[3] / 3;
     M.sR[k][5] = a[4] / 4;
+    {
+      const double gR[7] = {a[5], a[0] - a[6], -a[0], -a[1] / 2, -a[2] / 6, -a[3] / 12, -a[4] / 20};
+      for (int i = 0; i < 7; ++i) M.gR[k][i] = gR[i];
+    }
     for (int i = 0; i <= 100; ++i) {
       const double T = 200.0 + 33.0 * i;
       const double cp = a[0] + T * (a[1] + T * (a[2] + T * (a[3] + T * a[4])));
@@ -544,6 +596,15 @@ smc_status smc_create(const smc_grid *grid, const smc_mechanism *mech, const smc
   M.inv_T_ref = 1.0 / mech->T_ref;
   M.eta_exp = mech->eta_exp;
   M.inv_Pr = 1.0 / mech->Pr;
+  for (int k = 0; k < ns; ++k) {
+    for (int i = 0; i < 6; ++i) M.hTf[k][i] = (float)M.hT[k][i];
+    M.Ru_Wf[k] = (float)M.Ru_W[k];
+    M.invLef[k] = (float)M.invLe[k];
+  }
+  M.eta_ref_f = (float)M.eta_ref;
+  M.inv_T_ref_f = (float)M.inv_T_ref;
+  M.eta_exp_f = (float)M.eta_exp;
+  M.inv_Pr_f = (float)M.inv_Pr;
   h->hrx.resize(nr);
   for (int r = 0; r < nr; ++r) {
     Reaction &R = h->hrx[r];
@@ -559,11 +620,13 @@ smc_status smc_create(const smc_grid *grid, const smc_mechanism *mech, const smc
       if (f > 0) {
         if (R.nf == SMC_MAX_SIDE) return bail(fail(h, SMC_ERR_ARG, "more than 4 reactant species"));
         R.fk[R.nf] = k;
+        R.fcd[R.nf] = f;
         R.fc[R.nf++] = f;
       }
       if (p > 0) {
         if (R.nr_ == SMC_MAX_SIDE) return bail(fail(h, SMC_ERR_ARG, "more than 4 product species"));
         R.rk[R.nr_] = k;
+        R.rcd[R.nr_] = p;
         R.rc[R.nr_++] = p;
       }
       dnu += p - f;
@@ -577,6 +640,7 @@ smc_status smc_create(const smc_grid *grid, const smc_mechanism *mech, const smc
     for (int i = 0; i < R.nr_; ++i) mol_r += R.rc[i];
     if (mol_f > 3 || mol_r > 3) return bail(fail(h, SMC_ERR_ARG, "more than three molecules on a reaction side"));
     R.dnu = dnu;
+    R.dn = (int)dnu;
   }
   // ---- grid
   if (grid->nboxes < 1 || !grid->lo || !grid->hi) return bail(fail(h, SMC_ERR_ARG, "no boxes"));
@@ -697,6 +761,9 @@ smc_status smc_destroy(smc_handle *h) {
   cudaFree(h->d_gmap);
   cudaFree(h->d_imap);
   for (int d = 0; d < 3; ++d) cudaFree(h->d_lines[d]);
+  cudaFree(h->d_lines_xt);
+  cudaFree(h->d_Qt);
+  cudaFree(h->d_Gt);
   cudaFree(h->d_Q);
   cudaFree(h->d_G);
   cudaFree(h->d_divacc);

@@ -14,7 +14,9 @@ namespace smc {
 // arithmetic.  x is clamped to [-708, 709] (the normal range of the result).
 // About 13 FP64 operations; error within ~1 ulp.
 __device__ __forceinline__ double fast_exp(const Mech &m, double x) {
-  x = fmin(fmax(x, -708.0), 709.0);
+  // clamp only when |x| >= 512 (exponent field test in integer arithmetic;
+  // NaN also takes this branch and stays NaN)
+  if ((__double2hiint(x) & 0x7ff00000) >= ((1023 + 9) << 20)) x = fmin(fmax(x, -708.0), 709.0);
   const double shift = 6755399441055744.0;                 // 1.5 * 2^52
   const double t = x * 92.33248261689366;                  // 64 / ln 2
   const double nd = (t + shift) - shift;                   // nearest integer
@@ -52,6 +54,14 @@ __device__ __forceinline__ double sR(const Mech &m, int k, double T, double lnT)
   return c[0] * lnT + c[1] + T * (c[2] + T * (c[3] + T * (c[4] + T * c[5])));
 }
 
+// g/RT = h/RT - s/R of species k, folded into one polynomial in T plus the
+// 1/T and ln T terms (the same value as hR(T)/T - sR(T) in fewer operations).
+__device__ __forceinline__ double gRT(const Mech &m, int k, double T, double invT, double lnT) {
+  const double *c = m.gR[k];
+  const double poly = T * (c[3] + T * (c[4] + T * (c[5] + T * c[6])));
+  return fma(c[0], invT, fma(c[2], lnT, c[1] + poly));
+}
+
 // Temperature from the specific internal energy e and mass fractions Y:
 // Newton's method on sum_k Y_k e_k(T) = e, e_k = (R/W_k)(h_k/R - T), from the
 // first guess T0, stopping when |dT| <= tol |T|.  The species sums are folded
@@ -60,7 +70,8 @@ __device__ __forceinline__ double sR(const Mech &m, int k, double T, double lnT)
 // so every iteration costs one Horner evaluation of e and of de/dT = c_v.
 // Returns false if maxit steps did not converge.
 __device__ __forceinline__ bool newton_T(const Mech &m, const double *Y, double e, double T0,
-                                         double tol, int maxit, double &Tout) {
+                                         double tol, int maxit, double &Tout,
+                                         double *cp_mix = nullptr, double *h_mix = nullptr) {
   const int ns = m.ns;
   double H0 = 0.0, H1 = 0.0, H2 = 0.0, H3 = 0.0, H4 = 0.0, H5 = 0.0, yr_sum = 0.0;
   for (int k = 0; k < ns; ++k) {
@@ -78,18 +89,22 @@ __device__ __forceinline__ bool newton_T(const Mech &m, const double *Y, double 
   H1 -= yr_sum;
   const double D2 = 2.0 * H2, D3 = 3.0 * H3, D4 = 4.0 * H4, D5 = 5.0 * H5;
   double T = T0;
+  bool ok = false;
   for (int it = 0; it < maxit; ++it) {
     const double f = H0 + T * (H1 + T * (H2 + T * (H3 + T * (H4 + T * H5))));
     const double fp = H1 + T * (D2 + T * (D3 + T * (D4 + T * D5)));
     const double dT = f / fp;
     T -= dT;
     if (fabs(dT) <= tol * fabs(T)) {
-      Tout = T;
-      return true;
+      ok = true;
+      break;
     }
   }
   Tout = T;
-  return false;
+  // mixture c_p = d(sum Y_k h_k)/dT = c_v + sum Y_k R/W_k, and h = e(T) + (sum Y_k R/W_k) T
+  if (cp_mix) *cp_mix = H1 + T * (D2 + T * (D3 + T * (D4 + T * D5))) + yr_sum;
+  if (h_mix) *h_mix = H0 + T * (H1 + T * (H2 + T * (H3 + T * (H4 + T * H5)))) + e + yr_sum * T;
+  return ok;
 }
 
 // rho*omega_k (g/(cm^3 s)) by mass action with reversible Arrhenius rates and
@@ -114,7 +129,7 @@ __device__ __forceinline__ void production_rates(const Mech &m, const Reaction *
   const double invT = 1.0 / T;
   double gs = 0.0;
   for (int k = 0; k < ns; ++k) {
-    g[k] = hR(m, k, T) * invT - sR(m, k, T, lnT);   // g_k / (R T)
+    g[k] = gRT(m, k, T, invT, lnT);   // g_k / (R T)
     gs += g[k];
   }
   gs *= m.inv_ns;
@@ -133,15 +148,14 @@ __device__ __forceinline__ void production_rates(const Mech &m, const Reaction *
     double fwd = 1.0, rev = 1.0;
     for (int i = 0; i < R.nf; ++i) {
       const int k = R.fk[i];
-      ex -= R.fc[i] * g[k];
+      ex -= R.fcd[i] * g[k];
       for (int j = 0; j < R.fc[i]; ++j) fwd *= z[k];
     }
     for (int i = 0; i < R.nr_; ++i)
       for (int j = 0; j < R.rc[i]; ++j) rev *= z[R.rk[i]];
-    const int dn = (int)R.dnu;
-    const double q = fast_exp(m, ex) * (fwd - Ppow[dn + 4] * rev);
-    for (int i = 0; i < R.nf; ++i) wdot[R.fk[i]] -= R.fc[i] * q;
-    for (int i = 0; i < R.nr_; ++i) wdot[R.rk[i]] += R.rc[i] * q;
+    const double q = fast_exp(m, ex) * (fwd - Ppow[R.dn + 4] * rev);
+    for (int i = 0; i < R.nf; ++i) wdot[R.fk[i]] -= R.fcd[i] * q;
+    for (int i = 0; i < R.nr_; ++i) wdot[R.rk[i]] += R.rcd[i] * q;
   }
   for (int k = 0; k < ns; ++k) wdot[k] *= m.W[k];
 }

@@ -33,10 +33,26 @@ struct f2 {
   float h, l;
 };
 
+// Truncating double -> float conversion in integer arithmetic (keeps the
+// FP64 pipe free): the top 23 stored mantissa bits are kept; magnitudes below
+// the float normal range flush to zero.  Exact when x has at most 24
+// significant bits.
+__device__ __forceinline__ float trunc_float(double x) {
+  const long long b = __double_as_longlong(x);
+  const int e = (int)((b >> 52) & 0x7ff) - 1023 + 127;
+  const unsigned sign = (unsigned)((unsigned long long)b >> 63) << 31;
+  if (e <= 0) return __uint_as_float(sign);
+  if (e >= 255) return __uint_as_float(sign | 0x7f800000u);
+  return __uint_as_float(sign | ((unsigned)e << 23) | (unsigned)((b >> 29) & 0x7fffff));
+}
+
+// x = hi + lo with hi the truncation of x to 24 bits (exactly representable)
+// and lo the remainder truncated to 24 bits: about 48 significant bits, one
+// FP64 operation.
 __device__ __forceinline__ void put_pair(float *Qf, size_t NG, int plane, long long g, double x) {
-  const float h = __double2float_rn(x);
-  Qf[(size_t)plane * NG + g] = h;
-  Qf[(size_t)(plane + 1) * NG + g] = __double2float_rn(x - (double)h);
+  const double hd = __longlong_as_double(__double_as_longlong(x) & (long long)0xFFFFFFFFE0000000ULL);
+  Qf[(size_t)plane * NG + g] = trunc_float(hd);
+  Qf[(size_t)(plane + 1) * NG + g] = trunc_float(x - hd);
 }
 
 __device__ __forceinline__ f2 get_pair(const float *__restrict__ Qf, size_t NG, int plane,
@@ -83,34 +99,32 @@ __global__ void __launch_bounds__(128) k_prim_m(const DevState s, const double *
     double Y[SMC_MAX_NS];
     for (int k = 0; k < ns; ++k) Y[k] = U[(5 + k) * NI + src] * invrho;
     const double e = rhoE * invrho - 0.5 * (u * u + v * v + w * w);
-    double T;
-    const bool ok = newton_T(m, Y, e, s.opt.T0, s.opt.tol, s.opt.maxit, T);
+    double T, cpd, hm;
+    const bool ok = newton_T(m, Y, e, s.opt.T0, s.opt.tol, s.opt.maxit, T, &cpd, &hm);
     unsigned flag = 0;
     if (!ok) flag |= ST_NONCONV;
     if (!(rho > 0.0) || !(T > 0.0)) flag |= ST_NONPHYS;
     if (!isfinite(rho) || !isfinite(rhoE) || !isfinite(T)) flag |= ST_NONFINITE;
     if (flag) atomicOr(s.status, flag);
 
-    double wmix = 0.0, hm = 0.0;
-    float cpm = 0.0f;
-    const float Tf = (float)T;
+    double wmix = 0.0;
+    const float cpm = trunc_float(cpd);
+    const float Tf = trunc_float(T);
     float h32[SMC_MAX_NS];
     for (int k = 0; k < ns; ++k) {
       wmix += Y[k] * m.invW[k];
-      const double hk = m.Ru_W[k] * hR(m, k, T);
-      hm += Y[k] * hk;
-      h32[k] = (float)hk;
-      const float cp = (float)m.cp[k][0] + Tf * ((float)m.cp[k][1] + Tf * ((float)m.cp[k][2] +
-                       Tf * ((float)m.cp[k][3] + Tf * (float)m.cp[k][4])));
-      cpm += (float)Y[k] * (float)m.Ru_W[k] * cp;
+      // species enthalpies only enter coefficients: FP32
+      const float *c = m.hTf[k];
+      const float hRf = c[0] + Tf * (c[1] + Tf * (c[2] + Tf * (c[3] + Tf * (c[4] + Tf * c[5]))));
+      h32[k] = m.Ru_Wf[k] * hRf;
     }
     const double p = rho * kRu * T * wmix;
-    const float invp = 1.0f / (float)p;
+    const float invp = 1.0f / trunc_float(p);
     const double inv_wmix = 1.0 / wmix;
     // transport in FP32
-    const float eta = (float)m.eta_ref * __powf(Tf * (float)m.inv_T_ref, (float)m.eta_exp);
-    const float xi = (float)s.opt.xi_ratio * eta;
-    const float lam = cpm * eta * (float)m.inv_Pr;
+    const float eta = m.eta_ref_f * __powf(Tf * m.inv_T_ref_f, m.eta_exp_f);
+    const float xi = s.xi_ratio_f * eta;
+    const float lam = cpm * eta * m.inv_Pr_f;
     const float rd0 = lam / cpm;
     put_pair(Qf, NG, PM_U, g, u);
     put_pair(Qf, NG, PM_V, g, v);
@@ -131,8 +145,8 @@ __global__ void __launch_bounds__(128) k_prim_m(const DevState s, const double *
     float ap = 0.0f, sb = 0.0f;
     for (int k = 0; k < ns; ++k) {
       const double X = Y[k] * m.invW[k] * inv_wmix;
-      const float rd = rd0 * (float)m.invLe[k];
-      const float B = rd * (float)(X - Y[k]) * invp;
+      const float rd = rd0 * m.invLef[k];
+      const float B = rd * trunc_float(X - Y[k]) * invp;
       const float hp = h32[k] - href;
       if (mode == 0) {
         ap += h32[k] * B;

@@ -36,20 +36,18 @@ __global__ void __launch_bounds__(128) k_prim(const DevState s, const double *__
     double Y[SMC_MAX_NS], h[SMC_MAX_NS];
     for (int k = 0; k < ns; ++k) Y[k] = U[(5 + k) * NI + src] * invrho;
     const double e = rhoE * invrho - 0.5 * (u * u + v * v + w * w);
-    double T;
-    const bool ok = newton_T(m, Y, e, s.opt.T0, s.opt.tol, s.opt.maxit, T);
+    double T, cpm, hm;
+    const bool ok = newton_T(m, Y, e, s.opt.T0, s.opt.tol, s.opt.maxit, T, &cpm, &hm);
     unsigned flag = 0;
     if (!ok) flag |= ST_NONCONV;
     if (!(rho > 0.0) || !(T > 0.0)) flag |= ST_NONPHYS;
     if (!isfinite(rho) || !isfinite(rhoE) || !isfinite(T)) flag |= ST_NONFINITE;
     if (flag) atomicOr(s.status, flag);
 
-    double wmix = 0.0, cpm = 0.0, hm = 0.0;
+    double wmix = 0.0;
     for (int k = 0; k < ns; ++k) {
       wmix += Y[k] * m.invW[k];
       h[k] = m.Ru_W[k] * hR(m, k, T);
-      cpm += Y[k] * m.Ru_W[k] * cpR(m, k, T);
-      hm += Y[k] * h[k];
     }
     const double p = rho * kRu * T * wmix;
     const double invp = 1.0 / p;

@@ -2,6 +2,8 @@
 // linear combination of state and right-hand-side arrays, and the mode-1
 // multirate fine-node chain (Sec. 3.2, eq. mrupdate) in which every cell
 // advances through the reaction substeps of one coarse interval on its own.
+#include <algorithm>
+
 #include "chem.cuh"
 #include "smc_internal.h"
 
@@ -30,9 +32,10 @@ void launch_combo(const double *in, double *out, const Combo &cb, long long n, c
   k_combo<<<grid_for(n, 256), 256, 0, st>>>(in, out, cb, n);
 }
 
-// Reaction right-hand side f2 at one cell from its conserved state.
+// Reaction right-hand side f2 at one cell from its conserved state.  Tg is
+// the Newton first guess on entry and the temperature on return.
 __device__ __forceinline__ bool cell_reactions(const DevState &s, const double *Uc, double *f2,
-                                               unsigned &flag) {
+                                               unsigned &flag, double &Tg) {
   const Mech &m = *s.mech;
   const int ns = s.ns;
   const double rho = Uc[0];
@@ -42,7 +45,8 @@ __device__ __forceinline__ bool cell_reactions(const DevState &s, const double *
   for (int k = 0; k < ns; ++k) Y[k] = Uc[5 + k] * invrho;
   const double e = Uc[4] * invrho - 0.5 * (u * u + v * v + w * w);
   double T;
-  const bool ok = newton_T(m, Y, e, s.opt.T0, s.opt.tol, s.opt.maxit, T);
+  const bool ok = newton_T(m, Y, e, Tg, s.opt.tol, s.opt.maxit, T);
+  if (ok) Tg = T;
   if (!ok) flag |= ST_NONCONV;
   if (!(rho > 0.0) || !(T > 0.0)) flag |= ST_NONPHYS;
   if (!isfinite(rho) || !isfinite(T)) flag |= ST_NONFINITE;
@@ -63,7 +67,8 @@ __global__ void __launch_bounds__(128) k_chem_only(const DevState s, const doubl
     double Uc[5 + SMC_MAX_NS], f2[SMC_MAX_NS];
     for (int c = 0; c < nv; ++c) Uc[c] = U[(size_t)c * NI + i];
     unsigned flag = 0;
-    cell_reactions(s, Uc, f2, flag);
+    double Tg = s.opt.T0;
+    cell_reactions(s, Uc, f2, flag, Tg);
     if (flag) atomicOr(s.status, flag);
     for (int k = 0; k < ns; ++k) F2[(size_t)k * NI + i] = f2[k];
   }
@@ -87,9 +92,12 @@ __global__ void __launch_bounds__(128) k_fine_chain(const DevState s, const doub
     double Uc[5 + SMC_MAX_NS], f2[SMC_MAX_NS];
     for (int c = 0; c < nv; ++c) Uc[c] = Uin[(size_t)c * NI + i];
     unsigned flag = 0;
+    // each substep's Newton solve starts from the previous substep's
+    // temperature (a deterministic sequence within the chain)
+    double Tg = s.opt.T0;
     for (int sidx = 0; sidx < fc.nsub; ++sidx) {
       if (sidx > 0 || fc.eval_first) {
-        cell_reactions(s, Uc, f2, flag);
+        cell_reactions(s, Uc, f2, flag, Tg);
         for (int k = 0; k < ns; ++k) fc.F2new[sidx][(size_t)k * NI + i] = f2[k];
       } else {
         for (int k = 0; k < ns; ++k) f2[k] = fc.F2old[0][(size_t)k * NI + i];
@@ -109,11 +117,60 @@ __global__ void __launch_bounds__(128) k_fine_chain(const DevState s, const doub
       }
     }
     if (fc.eval_last) {
-      cell_reactions(s, Uc, f2, flag);
+      cell_reactions(s, Uc, f2, flag, Tg);
       for (int k = 0; k < ns; ++k) fc.F2new[fc.nsub][(size_t)k * NI + i] = f2[k];
     }
     if (flag) atomicOr(s.status, flag);
     for (int c = 0; c < nv; ++c) Uout[(size_t)c * NI + i] = Uc[c];
+  }
+}
+
+// [z][y][x] -> [x][z][y] within each ghosted box, 32 x 32 (x, y) tiles through
+// shared memory so that both the reads and the writes are coalesced.
+template <typename T>
+__global__ void __launch_bounds__(256) k_transpose_x(const Box *__restrict__ boxes, int nboxes,
+                                                     long long NG, const T *__restrict__ src,
+                                                     T *__restrict__ dst, int planes) {
+  __shared__ T tile[32][33];
+  const int b = blockIdx.z % nboxes;
+  const int plane = blockIdx.z / nboxes;
+  const Box B = boxes[b];
+  const int tilesx = (B.gx + 31) / 32, tilesy = (B.gy + 31) / 32;
+  const size_t pbase = (size_t)plane * NG + B.off_g;
+  for (long long t = blockIdx.x; t < (long long)tilesx * tilesy * B.gz; t += gridDim.x) {
+    const int z = (int)(t / ((long long)tilesx * tilesy));
+    const int r = (int)(t % ((long long)tilesx * tilesy));
+    const int x0 = (r % tilesx) * 32, y0 = (r / tilesx) * 32;
+    __syncthreads();
+    for (int j = threadIdx.y; j < 32; j += blockDim.y) {
+      const int x = x0 + threadIdx.x, y = y0 + j;
+      if (x < B.gx && y < B.gy)
+        tile[j][threadIdx.x] = src[pbase + ((size_t)z * B.gy + y) * B.gx + x];
+    }
+    __syncthreads();
+    for (int j = threadIdx.y; j < 32; j += blockDim.y) {
+      const int y = y0 + threadIdx.x, x = x0 + j;
+      if (x < B.gx && y < B.gy)
+        dst[pbase + ((size_t)x * B.gz + z) * B.gy + y] = tile[threadIdx.x][j];
+    }
+  }
+}
+
+void launch_transpose_x(const DevState &s, const void *src, void *dst, int planes, int esize,
+                        cudaStream_t st) {
+  dim3 block(32, 8);
+  // grid.z = boxes x planes, at most 65535 per launch
+  const int per = (int)std::max<long long>(1, 65535 / std::max(1, s.nboxes));
+  for (int p0 = 0; p0 < planes; p0 += per) {
+    const int np = std::min(per, planes - p0);
+    dim3 grid(64, 1, (unsigned)((long long)s.nboxes * np));
+    const size_t off = (size_t)p0 * s.nghost;
+    if (esize == 8)
+      k_transpose_x<double><<<grid, block, 0, st>>>(s.boxes, s.nboxes, s.nghost,
+                                                    (const double *)src + off, (double *)dst + off, np);
+    else
+      k_transpose_x<float><<<grid, block, 0, st>>>(s.boxes, s.nboxes, s.nghost,
+                                                   (const float *)src + off, (float *)dst + off, np);
   }
 }
 

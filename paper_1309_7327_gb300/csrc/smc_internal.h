@@ -29,17 +29,28 @@ struct Mech {
   double cp[SMC_MAX_NS][5];       // cp/R = c0 + c1 T + ... + c4 T^4
   double hT[SMC_MAX_NS][6];       // h/R  = a6 + T (a1 + T (a2/2 + ...))
   double sR[SMC_MAX_NS][6];       // s/R  = a1 ln T + a7 + T (a2 + T (a3/2 + ...)) : {a1, a7, a2, a3/2, a4/3, a5/4}
+  double gR[SMC_MAX_NS][7];       // g/RT = a6/T + (a1 - a7) - a1 ln T + T (-a2/2 + T (-a3/6 + T (-a4/12 + T (-a5/20))))
+                                  //   : {a6, a1 - a7, -a1, -a2/2, -a3/6, -a4/12, -a5/20}
   double eta_ref, inv_T_ref, eta_exp, inv_Pr;
   double inv_ns;
   double exp2tab[64];             // 2^(j/64), j = 0..63 (table of fast_exp)
+  // float copies for the mixed-precision transport (no conversions in kernels)
+  float hTf[SMC_MAX_NS][6];
+  float Ru_Wf[SMC_MAX_NS];
+  float invLef[SMC_MAX_NS];
+  float eta_ref_f, inv_T_ref_f, eta_exp_f, inv_Pr_f;
 };
 
 struct Reaction {
   double lnA, b, Ea_R;            // Ea / R_c (K)
   double dnu;                     // sum_k nu''_k - nu'_k
+  double fcd[SMC_MAX_SIDE];       // coefficients as doubles (no int->double
+  double rcd[SMC_MAX_SIDE];       //   conversions on the FP64 pipe)
   int nf, nr_;                    // species on each side
   int fk[SMC_MAX_SIDE], fc[SMC_MAX_SIDE];
   int rk[SMC_MAX_SIDE], rc[SMC_MAX_SIDE];
+  int dn;                         // dnu as an integer, -4..4
+  int pad;
 };
 
 // Geometry of one box in the ghosted (Q) and interior (U) layouts.
@@ -111,9 +122,11 @@ struct DevState {
   long long nlines[3];
   double *Q;                      // [nq][nghost]
   double *G;                      // [9][nghost] velocity gradients D_e u_c
+  double *Qt, *Gt;                // the same fields with x the slowest index in each box
   double *divacc;                 // [ncells] sum_k narrow species divergence
   unsigned *status;
   Opts opt;
+  float xi_ratio_f;
 };
 
 void launch_prim(const DevState &s, const double *U, cudaStream_t st);
@@ -121,6 +134,10 @@ void launch_grad(const DevState &s, cudaStream_t st);
 void launch_march(const DevState &s, int dir, double *dUdt, int first, cudaStream_t st);
 void launch_final(const DevState &s, double *dUdt, int transport, int chemistry, cudaStream_t st);
 void launch_prim_to_cons(const DevState &s, const double *prim, double *U, cudaStream_t st);
+// Copy `planes` planes of element size `esize` (4 or 8) from the box layout
+// [z][y][x] to [x][z][y] per ghosted box (for the x-direction stencil march).
+void launch_transpose_x(const DevState &s, const void *src, void *dst, int planes, int esize,
+                        cudaStream_t st);
 
 // Mixed precision (kernels_mixed.cu): FP32 stencils / transport on float-pair
 // scratch in the Q buffer, FP64 temperature, chemistry and accumulation.
