@@ -208,6 +208,27 @@ smc_status smc_collocation(int nodes, double *tau, double *S);
 smc_status smc_multirate_collocation(int coarse, int fine, double *t1, double *t2,
                                      double *S21, double *S22);
 
+/* The FP64 right-hand side of smc_rhs for ONE triply periodic box of
+ * n[0] x n[1] x n[2] cells (spacing dx, cm) without any device allocation.
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot call cudaMalloc -- code inside CUDA stream capture, applications
+ * whose framework owns all device memory in a fixed arena, and loops that
+ * must not pay the implicit synchronisation of cudaMalloc/cudaFree.
+ * U and dUdt are caller-owned device arrays in the box layout; mech is host
+ * memory.  Default options (correction-velocity mode, default stencil
+ * parameters, reactions on).  All scratch, tables and constants live in one
+ * static device array of 20 MiB that every GPU loading the library reserves
+ * until the process exits; a box whose scratch would not fit (about 16^3
+ * cells with 21 species, 24^3 with 3) returns SMC_ERR_ARG.  The first call
+ * on a device looks up that array's address (cudaGetSymbolAddress) and
+ * should come before any stream capture.  Tables are copied from host
+ * memory with cudaMemcpyAsync on `stream` (a cudaStream_t, NULL = default)
+ * and the call returns after the stream has finished, with the device
+ * status of the evaluation.  Calls share the array: calls that overlap on
+ * the GPU race and must be serialised by the caller. */
+smc_status smc_rhs_noalloc(const int n[3], const double dx[3], const smc_mechanism *mech,
+                           const double *U, double *dUdt, void *stream);
+
 /* Message describing the last error on this handle ("" if none).  The
  * string is owned by the handle. */
 const char *smc_last_error(smc_handle *h);

@@ -31,7 +31,8 @@ KERNELS = ["prim", "grad", "march", "final", "update", "fine", "chem", "other"]
 
 EXPORTS = ["smc_create", "smc_destroy", "smc_rhs", "smc_sdc_step", "smc_prim_to_cons",
            "smc_set_stream", "smc_set_option", "smc_get_stats", "smc_synchronize",
-           "smc_invalidate", "smc_collocation", "smc_multirate_collocation", "smc_last_error"]
+           "smc_invalidate", "smc_collocation", "smc_multirate_collocation", "smc_rhs_noalloc",
+           "smc_last_error"]
 
 
 class smc_grid(C.Structure):
@@ -79,6 +80,8 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
     lib.smc_invalidate.argtypes = [vp]
     lib.smc_collocation.argtypes = [C.c_int, vp, vp]
     lib.smc_multirate_collocation.argtypes = [C.c_int, C.c_int, vp, vp, vp, vp]
+    lib.smc_rhs_noalloc.argtypes = [C.POINTER(C.c_int), C.POINTER(C.c_double),
+                                    C.POINTER(smc_mechanism), vp, vp, vp]
     lib.smc_last_error.argtypes = [vp]
     lib.smc_last_error.restype = C.c_char_p
     for name in EXPORTS:
@@ -138,6 +141,33 @@ def smc_multirate_collocation(coarse: int, fine: int):
     if st != SMC_OK:
         raise SmcError(st, "smc_multirate_collocation")
     return t1, t2, S21, S22
+
+
+def smc_rhs_noalloc(n, dx, mech, U, dUdt, stream=None):
+    """The allocation-free right-hand side of one periodic box (see smc.h).
+    n, dx: 3-sequences; mech: a synth.Mechanism-like object; U, dUdt: CUDA
+    tensors in the box layout."""
+    keep = []
+
+    def arr(a, t):
+        a = np.ascontiguousarray(a, dtype=t)
+        keep.append(a)
+        return a.ctypes.data_as(C.POINTER(C.c_int if t == np.int32 else C.c_double))
+    m = smc_mechanism()
+    m.nspecies, m.nreactions = mech.ns, mech.nr
+    m.W, m.nasa7 = arr(mech.W, np.float64), arr(np.asarray(mech.nasa7).reshape(-1), np.float64)
+    m.nu_f = arr(np.asarray(mech.nu_f).reshape(-1), np.int32)
+    m.nu_r = arr(np.asarray(mech.nu_r).reshape(-1), np.int32)
+    m.A, m.b, m.Ea, m.Le = (arr(mech.A, np.float64), arr(mech.b, np.float64),
+                            arr(mech.Ea, np.float64), arr(mech.Le, np.float64))
+    m.eta_ref, m.T_ref, m.eta_exp, m.Pr = mech.eta_ref, mech.T_ref, mech.eta_exp, mech.Pr
+    nn = (C.c_int * 3)(*[int(v) for v in n])
+    dd = (C.c_double * 3)(*[float(v) for v in dx])
+    raw = getattr(stream, "cuda_stream", stream)
+    st = lib().smc_rhs_noalloc(nn, dd, C.byref(m), _ptr(U), _ptr(dUdt), C.c_void_p(raw))
+    if st != SMC_OK:
+        raise SmcError(st, "smc_rhs_noalloc")
+    return dUdt
 
 
 class SmcError(RuntimeError):
