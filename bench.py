@@ -274,6 +274,7 @@ def main():
         h.synchronize()
         del prim
         U0 = U.clone()
+        tuned = h.autotune(U)                 # segment length and x-line layout
         for _ in range(args.warmup):          # also fills the recycled f(U_0)
             h.sdc_step(U, wl.dt, nodes, sweeps, rsub)
         h.synchronize()
@@ -299,7 +300,7 @@ def main():
         launches = {k: st["launches"][k] - base["launches"][k] for k in st["launches"]}
         h.close()
         return dict(ms_step=ms / args.steps, launches=launches, kms=st["kernel_ms"],
-                    clocks=clocks, U0=U0)
+                    clocks=clocks, U0=U0, tuned=tuned)
 
     runs = {}
     if args.precision in ("mixed", "both"):
@@ -364,7 +365,7 @@ def main():
     else:
         hbm = None
     precision_report = {k: {"value": world * ncells * evals_per_step / (r["ms_step"] / 1e3) / 1e6,
-                            "ms_per_step": r["ms_step"],
+                            "ms_per_step": r["ms_step"], "autotuned": r["tuned"],
                             "kernel_ms_per_step": {kk: vv / args.steps for kk, vv in r["kms"].items()}}
                         for k, r in runs.items()}
     if "mixed" in runs and "fp64" in runs:
@@ -372,7 +373,8 @@ def main():
 
     # end to end: host buffers through the C ABI, copies inside the timed region
     Uh = U0.cpu().numpy().copy()
-    h2 = smc.Smc(wl.grid, wl.mech, {"precision": mixed_prec})
+    h2 = smc.Smc(wl.grid, wl.mech, {"precision": mixed_prec, "segment": R["tuned"]["segment"],
+                                    "x_layout": R["tuned"]["x_layout"]})
     h2.sdc_step(Uh, wl.dt, nodes, sweeps, rsub)
     e2e_steps = max(1, min(args.steps, 3))
     t0 = time.perf_counter()

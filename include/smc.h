@@ -117,7 +117,11 @@ enum {
   SMC_OPT_T_GUESS = 8,         /* Newton first guess in K (default 1000) */
   SMC_OPT_REACTIONS = 9,       /* 1: include rho*omega_k (default); 0: omit */
   SMC_OPT_SEGMENT = 10,        /* cells per thread along a stencil line (default 16) */
-  SMC_OPT_PROFILE = 11         /* 1: time every kernel launch with CUDA events (default 0) */
+  SMC_OPT_PROFILE = 11,        /* 1: time every kernel launch with CUDA events (default 0) */
+  SMC_OPT_USE_GRAPHS = 12,     /* 1 (default): replay recycled steps as one CUDA graph when the
+                                  handle has a non-default stream; 0: launch kernels one by one */
+  SMC_OPT_X_LAYOUT = 13        /* x-direction lines of the current precision: 0 read the box
+                                  layout, 1 read an x-slowest copy (default 0 FP64, 1 mixed) */
 };
 
 /* Kernel classes counted in smc_stats (launches always; times only while
@@ -195,6 +199,15 @@ smc_status smc_synchronize(smc_handle *h);
 
 /* Drop the cached f(U_0) of the last step. */
 smc_status smc_invalidate(smc_handle *h);
+
+/* Autotune the stencil kernels for the handle's current precision: time
+ * one right-hand-side evaluation at U (device memory, box layout) for every
+ * segment length (cells per thread along a stencil line: 8, 16, 32, 64) and
+ * both layouts of the x-direction lines (0: read the box layout directly;
+ * 1: read a copy with x the slowest index, made once per evaluation), and
+ * keep the fastest.  *segment and *x_layout (may be NULL) receive the choice.
+ * Synchronises the handle's stream. */
+smc_status smc_autotune(smc_handle *h, const double *U, int *segment, int *x_layout);
 
 /* Collocation data used by smc_sdc_step (host computation, no GPU needed).
  * smc_collocation: the `nodes` Gauss-Lobatto nodes on [0, 1] (tau[nodes])

@@ -24,6 +24,7 @@ struct smc_handle {
   Opts opt;
   int precision = 0;
   int segment = 16;
+  int xt[2] = {0, 1};                   // x lines on the x-slowest copy (FP64, mixed)
   cudaStream_t stream = 0;
   int device = 0;
 
@@ -35,6 +36,7 @@ struct smc_handle {
   LineItem *d_lines[3] = {nullptr, nullptr, nullptr};
   long long nlines[3] = {0, 0, 0};
   LineItem *d_lines_xt = nullptr;       // x lines in the x-slowest (transposed) layout
+  long long *d_xt_tiles = nullptr;      // per-box prefix of transpose tiles
   double *d_Qt = nullptr, *d_Gt = nullptr;
   double *d_Q = nullptr, *d_G = nullptr, *d_divacc = nullptr;
   unsigned *d_status = nullptr;
@@ -51,6 +53,19 @@ struct smc_handle {
   int cache_kind = 0;                   // 0 none, 1 single-rate, 2 multirate
   int cache_f = -1, cache_r = -1;
 
+  // CUDA graph of one recycled time step (replayed while the key matches)
+  int use_graphs = 1;
+  int opt_version = 0;
+  cudaGraphExec_t graph_exec = nullptr;
+  struct GraphKey {
+    const void *U;
+    double dt;
+    int nodes, sweeps, rsub, precision, opt_version;
+  } graph_key = {nullptr, 0.0, 0, 0, 0, 0, -1};
+  long long graph_d_rhs = 0, graph_d_react = 0;
+  long long graph_d_launch[SMC_NKERNELS] = {};
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> graph_events;
+
   long long n_rhs = 0, n_react = 0, n_steps = 0;
   long long launches[SMC_NKERNELS] = {};
   double kernel_ms[SMC_NKERNELS] = {};
@@ -63,6 +78,8 @@ struct smc_handle {
 };
 
 namespace {
+
+void drop_graph(smc_handle *h);
 
 smc_status fail(smc_handle *h, smc_status st, const std::string &msg) {
   if (h) h->err = msg;
@@ -149,6 +166,7 @@ DevState state(smc_handle *h) {
   s.G = h->d_G;
   s.Qt = h->d_Qt;
   s.Gt = h->d_Gt;
+  s.xt_tiles = h->d_xt_tiles;
   s.divacc = h->d_divacc;
   s.status = h->d_status;
   s.opt = h->opt;
@@ -320,45 +338,49 @@ smc_status ensure_pools(smc_handle *h, int nf, int nr) {
 smc_status eval_rhs(smc_handle *h, const double *U, double *F, int transport, int chemistry) {
   DevState s = state(h);
   const int chem = chemistry && h->opt.reactions && h->nr > 0;
-  if (h->precision == 1) {
-    if (!h->d_dUf) CUDA_TRY(h, dalloc(h, &h->d_dUf, (size_t)h->nv * h->ncells));
-    if (!h->d_Qt) {
-      // float planes: the x-slowest copy of Q and of the gradients
-      CUDA_TRY(h, dalloc(h, reinterpret_cast<float **>(&h->d_Qt), (size_t)nQm(h->ns) * h->nghost));
-      CUDA_TRY(h, dalloc(h, reinterpret_cast<float **>(&h->d_Gt), (size_t)9 * h->nghost));
-      s = state(h);
+  const int mixed = h->precision == 1;
+  const bool xt = h->xt[mixed] != 0;
+  if (xt && !h->d_Qt) {
+    // the x-slowest copy of Q and of the gradients (sized for FP64 planes)
+    CUDA_TRY(h, dalloc(h, &h->d_Qt, (size_t)nQ(h->ns) * h->nghost));
+    CUDA_TRY(h, dalloc(h, &h->d_Gt, (size_t)9 * h->nghost));
+    s = state(h);
+  }
+  if (mixed && !h->d_dUf) CUDA_TRY(h, dalloc(h, &h->d_dUf, (size_t)h->nv * h->ncells));
+  {
+    Timed t(h, SMC_K_PRIM);
+    if (mixed) launch_prim_m(s, U, h->stream); else launch_prim(s, U, h->stream);
+  }
+  if (transport) {
+    {
+      Timed t(h, SMC_K_GRAD);
+      if (mixed) launch_grad_m(s, h->stream); else launch_grad(s, h->stream);
     }
-    { Timed t(h, SMC_K_PRIM); launch_prim_m(s, U, h->stream); }
-    if (transport) {
-      { Timed t(h, SMC_K_GRAD); launch_grad_m(s, h->stream); }
-      {
-        // x lines read a copy with x the slowest index, so that consecutive
-        // threads (consecutive y) read consecutive addresses
-        { Timed t(h, SMC_K_OTHER); launch_transpose_x(s, s.Q, s.Qt, nQm(h->ns), 4, h->stream); }
-        Timed t(h, SMC_K_OTHER);
-        launch_transpose_x(s, reinterpret_cast<float *>(s.G) + 3 * (size_t)h->nghost,
-                           reinterpret_cast<float *>(s.Gt) + 3 * (size_t)h->nghost, 6, 4, h->stream);
-      }
-      DevState sx = s;
+    DevState sx = s;
+    if (xt) {
+      // x lines read a copy with x the slowest index, so that consecutive
+      // threads (consecutive y) read consecutive addresses
+      const int es = mixed ? 4 : 8;
+      const int planes = mixed ? nQm(h->ns) : nQ(h->ns);
+      { Timed t(h, SMC_K_OTHER); launch_transpose_x(s, s.Q, s.Qt, planes, es, h->stream); }
+      Timed t(h, SMC_K_OTHER);
+      launch_transpose_x(s, reinterpret_cast<char *>(s.G) + (size_t)3 * h->nghost * es,
+                         reinterpret_cast<char *>(s.Gt) + (size_t)3 * h->nghost * es, 6, es,
+                         h->stream);
       sx.Q = s.Qt;
       sx.G = s.Gt;
       sx.lines[0] = h->d_lines_xt;
-      for (int d = 0; d < 3; ++d) {
-        Timed t(h, SMC_K_MARCH);
-        launch_march_m(d == 0 ? sx : s, d, h->d_dUf, d == 0, h->stream);
-      }
     }
+    for (int d = 0; d < 3; ++d) {
+      Timed t(h, SMC_K_MARCH);
+      if (mixed) launch_march_m(d == 0 ? sx : s, d, h->d_dUf, d == 0, h->stream);
+      else launch_march(d == 0 ? sx : s, d, F, d == 0, h->stream);
+    }
+  }
+  if (mixed) {
     { Timed t(h, SMC_K_FINAL); launch_final_m(s, U, h->d_dUf, F, transport, chem, h->stream); }
     CUDA_TRY(h, cudaGetLastError());
     return SMC_OK;
-  }
-  { Timed t(h, SMC_K_PRIM); launch_prim(s, U, h->stream); }
-  if (transport) {
-    { Timed t(h, SMC_K_GRAD); launch_grad(s, h->stream); }
-    for (int d = 0; d < 3; ++d) {
-      Timed t(h, SMC_K_MARCH);
-      launch_march(s, d, F, d == 0, h->stream);
-    }
   }
   { Timed t(h, SMC_K_FINAL); launch_final(s, F, transport, chem, h->stream); }
   CUDA_TRY(h, cudaGetLastError());
@@ -419,10 +441,15 @@ smc_status sdc_single_rate(smc_handle *h, double *U, const void *key, double dt,
     fold = fnew;
     set ^= 1;
   }
+  // keep f(U_M) in slot 0 so that every recycled step issues the same
+  // launches on the same buffers (the step can then be replayed as a graph)
+  if (fold[M] != 0)
+    CUDA_TRY(h, cudaMemcpyAsync(h->fpool[0], h->fpool[fold[M]], n * sizeof(double),
+                                cudaMemcpyDeviceToDevice, h->stream));
   CUDA_TRY(h, cudaGetLastError());
   h->cache_kind = 1;
   h->cache_U = (const double *)key;
-  h->cache_f = fold[M];
+  h->cache_f = 0;
   h->cache_r = -1;
   return SMC_OK;
 }
@@ -500,11 +527,18 @@ smc_status sdc_multirate(smc_handle *h, double *U, const void *key, double dt, i
     f2old = f2new;
     set ^= 1;
   }
+  if (f1old[M1] != 0)
+    CUDA_TRY(h, cudaMemcpyAsync(h->fpool[0], h->fpool[f1old[M1]], n * sizeof(double),
+                                cudaMemcpyDeviceToDevice, h->stream));
+  if (f2old[M2] != 0)
+    CUDA_TRY(h, cudaMemcpyAsync(h->rpool[0], h->rpool[f2old[M2]],
+                                (size_t)h->ns * h->ncells * sizeof(double), cudaMemcpyDeviceToDevice,
+                                h->stream));
   CUDA_TRY(h, cudaGetLastError());
   h->cache_kind = 2;
   h->cache_U = (const double *)key;
-  h->cache_f = f1old[M1];
-  h->cache_r = f2old[M2];
+  h->cache_f = 0;
+  h->cache_r = 0;
   return SMC_OK;
 }
 
@@ -576,7 +610,7 @@ smc_status smc_create(const smc_grid *grid, const smc_mechanism *mech, const smc
   if (!(mech->eta_ref > 0) || !(mech->T_ref > 0) || !(mech->Pr > 0))
     return bail(fail(h, SMC_ERR_ARG, "transport parameters must be positive"));
   M.inv_ns = 1.0 / ns;
-  for (int j = 0; j < 64; ++j) M.exp2tab[j] = (double)exp2l((long double)j / 64.0L);
+  for (int j = 0; j < 256; ++j) M.exp2tab[j] = (double)exp2l((long double)j / 256.0L);
   for (int i = 0; i <= 100; ++i) {
     // the production-rate evaluation needs the species' g/RT to spread over
     // less than 400 (see production_rates)
@@ -621,12 +655,14 @@ smc_status smc_create(const smc_grid *grid, const smc_mechanism *mech, const smc
         if (R.nf == SMC_MAX_SIDE) return bail(fail(h, SMC_ERR_ARG, "more than 4 reactant species"));
         R.fk[R.nf] = k;
         R.fcd[R.nf] = f;
+        R.fcw[R.nf] = f * mech->W[k];
         R.fc[R.nf++] = f;
       }
       if (p > 0) {
         if (R.nr_ == SMC_MAX_SIDE) return bail(fail(h, SMC_ERR_ARG, "more than 4 product species"));
         R.rk[R.nr_] = k;
         R.rcd[R.nr_] = p;
+        R.rcw[R.nr_] = p * mech->W[k];
         R.rc[R.nr_++] = p;
       }
       dnu += p - f;
@@ -745,6 +781,16 @@ smc_status smc_create(const smc_grid *grid, const smc_mechanism *mech, const smc
   TRY_ALLOC(cudaMemset(h->d_G, 0, (size_t)9 * h->nghost * sizeof(double)));
   TRY_ALLOC(dalloc(h, &h->d_divacc, (size_t)h->ncells));
   TRY_ALLOC(dalloc(h, &h->d_status, 1));
+  {
+    std::vector<long long> tiles(h->nboxes + 1, 0);
+    for (int b = 0; b < h->nboxes; ++b) {
+      const Box &B = h->boxes[b];
+      tiles[b + 1] = tiles[b] + (long long)((B.gx + 31) / 32) * ((B.gy + 31) / 32) * B.gz;
+    }
+    TRY_ALLOC(dalloc(h, &h->d_xt_tiles, tiles.size()));
+    TRY_ALLOC(cudaMemcpy(h->d_xt_tiles, tiles.data(), tiles.size() * sizeof(long long),
+                         cudaMemcpyHostToDevice));
+  }
   TRY_ALLOC(cudaMemset(h->d_status, 0, sizeof(unsigned)));
   smc_status st = build_lines(h);
   if (st) return bail(st);
@@ -762,6 +808,7 @@ smc_status smc_destroy(smc_handle *h) {
   cudaFree(h->d_imap);
   for (int d = 0; d < 3; ++d) cudaFree(h->d_lines[d]);
   cudaFree(h->d_lines_xt);
+  cudaFree(h->d_xt_tiles);
   cudaFree(h->d_Qt);
   cudaFree(h->d_Gt);
   cudaFree(h->d_Q);
@@ -773,6 +820,7 @@ smc_status smc_destroy(smc_handle *h) {
   cudaFree(h->d_U0);
   cudaFree(h->d_dUf);
   for (int i = 0; i < 3; ++i) cudaFree(h->d_stage[i]);
+  drop_graph(h);
   for (auto &p : h->ev_pending) {
     h->ev_free.push_back(p.second.first);
     h->ev_free.push_back(p.second.second);
@@ -807,6 +855,90 @@ smc_status smc_rhs(smc_handle *h, const double *U, double *dUdt) {
   return SMC_OK;
 }
 
+}  // extern "C"
+
+namespace {
+
+smc_status step_body(smc_handle *h, double *Ud, const void *key, double dt, int nodes, int sweeps,
+                     int rsub) {
+  return rsub <= 1 ? sdc_single_rate(h, Ud, key, dt, nodes, sweeps)
+                   : sdc_multirate(h, Ud, key, dt, nodes, sweeps, rsub);
+}
+
+void drop_graph(smc_handle *h) {
+  if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
+  h->graph_exec = nullptr;
+  for (auto &p : h->graph_events) {
+    h->ev_free.push_back(p.second.first);
+    h->ev_free.push_back(p.second.second);
+  }
+  h->graph_events.clear();
+  h->graph_key.opt_version = -1;
+}
+
+// A recycled step (f(U_0) cached in slot 0) launches the same kernels on the
+// same buffers every time, so it is captured once as a CUDA graph and
+// replayed while (U, dt, nodes, sweeps, substeps, options) are unchanged.
+smc_status graph_step(smc_handle *h, double *Ud, const void *key, double dt, int nodes,
+                      int sweeps, int rsub) {
+  const smc_handle::GraphKey k = {Ud, dt, nodes, sweeps, rsub, h->precision, h->opt_version};
+  const bool match = h->graph_exec && k.U == h->graph_key.U && k.dt == h->graph_key.dt &&
+                     k.nodes == h->graph_key.nodes && k.sweeps == h->graph_key.sweeps &&
+                     k.rsub == h->graph_key.rsub && k.precision == h->graph_key.precision &&
+                     k.opt_version == h->graph_key.opt_version;
+  if (!match) {
+    drop_graph(h);
+    const long long r0 = h->n_rhs, q0 = h->n_react;
+    long long l0[SMC_NKERNELS];
+    for (int i = 0; i < SMC_NKERNELS; ++i) l0[i] = h->launches[i];
+    const size_t ev0 = h->ev_pending.size();
+    CUDA_TRY(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+    smc_status st = step_body(h, Ud, key, dt, nodes, sweeps, rsub);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ec = cudaStreamEndCapture(h->stream, &graph);
+    if (st) {
+      if (graph) cudaGraphDestroy(graph);
+      return st;
+    }
+    if (ec != cudaSuccess) return fail(h, SMC_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(ec));
+    const cudaError_t ei = cudaGraphInstantiate(&h->graph_exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ei != cudaSuccess) {
+      h->graph_exec = nullptr;
+      return fail(h, SMC_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(ei));
+    }
+    // what one replay does to the counters; events recorded during capture
+    // belong to the graph now
+    h->graph_d_rhs = h->n_rhs - r0;
+    h->graph_d_react = h->n_react - q0;
+    for (int i = 0; i < SMC_NKERNELS; ++i) h->graph_d_launch[i] = h->launches[i] - l0[i];
+    h->n_rhs = r0;
+    h->n_react = q0;
+    for (int i = 0; i < SMC_NKERNELS; ++i) h->launches[i] = l0[i];
+    h->graph_events.assign(h->ev_pending.begin() + ev0, h->ev_pending.end());
+    h->ev_pending.resize(ev0);
+    h->graph_key = k;
+  }
+  CUDA_TRY(h, cudaGraphLaunch(h->graph_exec, h->stream));
+  h->n_rhs += h->graph_d_rhs;
+  h->n_react += h->graph_d_react;
+  for (int i = 0; i < SMC_NKERNELS; ++i) h->launches[i] += h->graph_d_launch[i];
+  if (h->profile && !h->graph_events.empty()) {
+    // the graph's events are overwritten by the next replay: read them now
+    CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    for (auto &p : h->graph_events) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, p.second.first, p.second.second) == cudaSuccess)
+        h->kernel_ms[p.first] += ms;
+    }
+  }
+  return SMC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
 smc_status smc_sdc_step(smc_handle *h, double *U, double dt, int nodes, int sweeps,
                         int reaction_substeps) {
   if (!h || !h->d_Q) return SMC_ERR_STATE;
@@ -826,10 +958,12 @@ smc_status smc_sdc_step(smc_handle *h, double *U, double dt, int nodes, int swee
     Ud = h->d_stage[2];
   }
   // the recycled f(U_0) is keyed by the caller's pointer (host or device)
-  if (reaction_substeps <= 1)
-    st = sdc_single_rate(h, Ud, U, dt, nodes, sweeps);
+  const bool recycled = h->cache_U == (const double *)U && h->cache_f == 0 &&
+                        h->cache_kind == (reaction_substeps <= 1 ? 1 : 2);
+  if (recycled && h->use_graphs && h->stream != 0)
+    st = graph_step(h, Ud, U, dt, nodes, sweeps, reaction_substeps);
   else
-    st = sdc_multirate(h, Ud, U, dt, nodes, sweeps, reaction_substeps);
+    st = step_body(h, Ud, U, dt, nodes, sweeps, reaction_substeps);
   if (st) return st;
   h->n_steps++;
   if (!dev) {
@@ -866,12 +1000,14 @@ smc_status smc_prim_to_cons(smc_handle *h, const double *prim, double *U) {
 smc_status smc_set_stream(smc_handle *h, void *stream) {
   if (!h) return SMC_ERR_STATE;
   h->stream = (cudaStream_t)stream;
+  h->opt_version++;
   return SMC_OK;
 }
 
 smc_status smc_set_option(smc_handle *h, int key, double v) {
   if (!h) return SMC_ERR_STATE;
   h->cache_kind = 0;
+  h->opt_version++;
   switch (key) {
     case SMC_OPT_PRECISION:
       if (v != 0.0 && v != 1.0) return fail(h, SMC_ERR_ARG, "precision must be 0 or 1");
@@ -901,6 +1037,11 @@ smc_status smc_set_option(smc_handle *h, int key, double v) {
       h->opt.T0 = v;
       return SMC_OK;
     case SMC_OPT_REACTIONS: h->opt.reactions = v != 0.0; return SMC_OK;
+    case SMC_OPT_USE_GRAPHS: h->use_graphs = v != 0.0; return SMC_OK;
+    case SMC_OPT_X_LAYOUT:
+      if (v != 0.0 && v != 1.0) return fail(h, SMC_ERR_ARG, "x layout must be 0 or 1");
+      h->xt[h->precision == 1] = (int)v;
+      return SMC_OK;
     case SMC_OPT_PROFILE:
       cudaStreamSynchronize(h->stream);
       collect_times(h);
@@ -947,6 +1088,51 @@ smc_status smc_invalidate(smc_handle *h) {
   h->cache_kind = 0;
   h->cache_U = nullptr;
   return SMC_OK;
+}
+
+smc_status smc_autotune(smc_handle *h, const double *U, int *segment, int *x_layout) {
+  if (!h || !h->d_Q) return SMC_ERR_STATE;
+  if (!U || !is_device_ptr(U)) return fail(h, SMC_ERR_ARG, "autotune needs U in device memory");
+  smc_status st = ensure_pools(h, 1, 0);
+  if (st) return st;
+  double *F = h->fpool[0];
+  h->cache_kind = 0;   // slot 0 is overwritten
+  const int mixed = h->precision == 1;
+  const int seg0 = h->segment, xt0 = h->xt[mixed];
+  const int segs[4] = {8, 16, 32, 64};
+  float best = 1e30f;
+  int best_seg = seg0, best_xt = xt0;
+  cudaEvent_t a, b;
+  CUDA_TRY(h, cudaEventCreate(&a));
+  CUDA_TRY(h, cudaEventCreate(&b));
+  for (int si = 0; si < 4; ++si)
+    for (int x = 0; x < 2; ++x) {
+      h->segment = segs[si];
+      h->xt[mixed] = x;
+      if ((st = build_lines(h))) return st;
+      if ((st = eval_rhs(h, U, F, 1, 1))) return st;      // warm-up (allocations)
+      CUDA_TRY(h, cudaEventRecord(a, h->stream));
+      for (int r = 0; r < 2; ++r)
+        if ((st = eval_rhs(h, U, F, 1, 1))) return st;
+      CUDA_TRY(h, cudaEventRecord(b, h->stream));
+      CUDA_TRY(h, cudaEventSynchronize(b));
+      float ms = 0.f;
+      CUDA_TRY(h, cudaEventElapsedTime(&ms, a, b));
+      if (ms < best) {
+        best = ms;
+        best_seg = segs[si];
+        best_xt = x;
+      }
+    }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  h->segment = best_seg;
+  h->xt[mixed] = best_xt;
+  if ((st = build_lines(h))) return st;
+  h->opt_version++;
+  if (segment) *segment = best_seg;
+  if (x_layout) *x_layout = best_xt;
+  return check_flags(h);
 }
 
 smc_status smc_collocation(int nodes, double *tau, double *S) {

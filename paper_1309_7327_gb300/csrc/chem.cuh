@@ -6,31 +6,30 @@
 namespace smc {
 
 // exp(x) in FP64 by the table-driven method of P. T. P. Tang (ACM TOMS 15,
-// 1989): x = (64 k + j) ln2/64 + r with |r| <= ln2/128, so that
-//   exp(x) = 2^k * 2^(j/64) * exp(r),
-// 2^(j/64) from a 64-entry table and exp(r) - 1 from its Taylor polynomial
-// to r^5 (truncation r^6/720 < 4e-17 relative).  n = 64 k + j is rounded with
+// 1989): x = (256 k + j) ln2/256 + r with |r| <= ln2/512, so that
+//   exp(x) = 2^k * 2^(j/256) * exp(r),
+// 2^(j/256) from a 256-entry table and exp(r) - 1 from its Taylor polynomial
+// to r^4 (truncation r^5/120 < 4e-17 relative).  n = 256 k + j is rounded with
 // the 1.5 * 2^52 shift, and 2^k is applied to the exponent field with integer
-// arithmetic.  x is clamped to [-708, 709] (the normal range of the result).
-// About 13 FP64 operations; error within ~1 ulp.
+// arithmetic.  |x| >= 512 is clamped to [-708, 709] (the normal range of the
+// result).  About 11 FP64 operations; error within ~1 ulp.
 __device__ __forceinline__ double fast_exp(const Mech &m, double x) {
   // clamp only when |x| >= 512 (exponent field test in integer arithmetic;
   // NaN also takes this branch and stays NaN)
   if ((__double2hiint(x) & 0x7ff00000) >= ((1023 + 9) << 20)) x = fmin(fmax(x, -708.0), 709.0);
   const double shift = 6755399441055744.0;                 // 1.5 * 2^52
-  const double t = x * 92.33248261689366;                  // 64 / ln 2
+  const double t = x * 369.3299304675746;                  // 256 / ln 2
   const double nd = (t + shift) - shift;                   // nearest integer
   const int n = __double2loint(t + shift);
-  // ln2/64 split: L1 has trailing zero bits so nd * L1 is exact for |n| < 2^18
-  const double L1 = 0.010830424696223417, L2 = 2.572804622327669e-14;
+  // ln2/256 split: L1 has 19 trailing zero bits so nd * L1 is exact for |n| < 2^19
+  const double L1 = 0.002707606173999011, L2 = 6.327543041662719e-14;
   const double r = fma(-nd, L2, fma(-nd, L1, x));
-  double q = 1.0 / 120.0;
-  q = fma(q, r, 1.0 / 24.0);
+  double q = 1.0 / 24.0;
   q = fma(q, r, 1.0 / 6.0);
   q = fma(q, r, 0.5);
   const double p = fma(r * r, q, r);                       // exp(r) - 1
-  const int j = n & 63;
-  const int k = n >> 6;                                    // floor division
+  const int j = n & 255;
+  const int k = n >> 8;                                    // floor division
   const double tj = m.exp2tab[j];
   const double y = fma(tj, p, tj);
   return __hiloint2double(__double2hiint(y) + (k << 20), __double2loint(y));
@@ -122,7 +121,7 @@ __device__ __forceinline__ bool newton_T(const Mech &m, const double *Y, double 
 // molecules per reaction side.
 __device__ __forceinline__ void production_rates(const Mech &m, const Reaction *__restrict__ rx,
                                                  double rho, double T, const double *Y,
-                                                 double *wdot) {
+                                                 double *wdot, const double *rhoY = nullptr) {
   const int ns = m.ns;
   double z[SMC_MAX_NS], g[SMC_MAX_NS];
   const double lnT = log(T);
@@ -135,7 +134,8 @@ __device__ __forceinline__ void production_rates(const Mech &m, const Reaction *
   gs *= m.inv_ns;
   for (int k = 0; k < ns; ++k) {
     g[k] -= gs;
-    z[k] = rho * Y[k] * m.invW[k] * fast_exp(m, g[k]);
+    const double c = (rhoY ? rhoY[k] : rho * Y[k]) * m.invW[k];
+    z[k] = c * fast_exp(m, g[k]);
     wdot[k] = 0.0;
   }
   // P^j for j = -4..4
@@ -153,11 +153,10 @@ __device__ __forceinline__ void production_rates(const Mech &m, const Reaction *
     }
     for (int i = 0; i < R.nr_; ++i)
       for (int j = 0; j < R.rc[i]; ++j) rev *= z[R.rk[i]];
-    const double q = fast_exp(m, ex) * (fwd - Ppow[R.dn + 4] * rev);
-    for (int i = 0; i < R.nf; ++i) wdot[R.fk[i]] -= R.fcd[i] * q;
-    for (int i = 0; i < R.nr_; ++i) wdot[R.rk[i]] += R.rcd[i] * q;
+    const double q = fast_exp(m, ex) * fma(-Ppow[R.dn + 4], rev, fwd);
+    for (int i = 0; i < R.nf; ++i) wdot[R.fk[i]] = fma(-R.fcw[i], q, wdot[R.fk[i]]);
+    for (int i = 0; i < R.nr_; ++i) wdot[R.rk[i]] = fma(R.rcw[i], q, wdot[R.rk[i]]);
   }
-  for (int k = 0; k < ns; ++k) wdot[k] *= m.W[k];
 }
 
 }  // namespace smc

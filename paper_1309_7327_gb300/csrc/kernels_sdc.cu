@@ -51,7 +51,7 @@ __device__ __forceinline__ bool cell_reactions(const DevState &s, const double *
   if (!(rho > 0.0) || !(T > 0.0)) flag |= ST_NONPHYS;
   if (!isfinite(rho) || !isfinite(T)) flag |= ST_NONFINITE;
   if (s.opt.reactions && m.nr > 0) {
-    production_rates(m, s.rx, rho, T, Y, f2);
+    production_rates(m, s.rx, rho, T, Y, f2, Uc + 5);
   } else {
     for (int k = 0; k < ns; ++k) f2[k] = 0.0;
   }
@@ -126,21 +126,31 @@ __global__ void __launch_bounds__(128) k_fine_chain(const DevState s, const doub
 }
 
 // [z][y][x] -> [x][z][y] within each ghosted box, 32 x 32 (x, y) tiles through
-// shared memory so that both the reads and the writes are coalesced.
+// shared memory so that both the reads and the writes are coalesced.  The
+// (plane, box, z, tile) work items are enumerated in one flat grid-stride loop.
 template <typename T>
 __global__ void __launch_bounds__(256) k_transpose_x(const Box *__restrict__ boxes, int nboxes,
+                                                     const long long *__restrict__ tiles,
                                                      long long NG, const T *__restrict__ src,
                                                      T *__restrict__ dst, int planes) {
   __shared__ T tile[32][33];
-  const int b = blockIdx.z % nboxes;
-  const int plane = blockIdx.z / nboxes;
-  const Box B = boxes[b];
-  const int tilesx = (B.gx + 31) / 32, tilesy = (B.gy + 31) / 32;
-  const size_t pbase = (size_t)plane * NG + B.off_g;
-  for (long long t = blockIdx.x; t < (long long)tilesx * tilesy * B.gz; t += gridDim.x) {
+  const long long per_plane = tiles[nboxes];
+  const long long total = per_plane * planes;
+  for (long long w = blockIdx.x; w < total; w += gridDim.x) {
+    const int plane = (int)(w / per_plane);
+    const long long r = w - (long long)plane * per_plane;
+    int lo = 0, hi = nboxes - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (tiles[mid] <= r) lo = mid; else hi = mid - 1;
+    }
+    const Box B = boxes[lo];
+    const long long t = r - tiles[lo];
+    const int tilesx = (B.gx + 31) / 32, tilesy = (B.gy + 31) / 32;
     const int z = (int)(t / ((long long)tilesx * tilesy));
-    const int r = (int)(t % ((long long)tilesx * tilesy));
-    const int x0 = (r % tilesx) * 32, y0 = (r / tilesx) * 32;
+    const int rr = (int)(t % ((long long)tilesx * tilesy));
+    const int x0 = (rr % tilesx) * 32, y0 = (rr / tilesx) * 32;
+    const size_t pbase = (size_t)plane * NG + B.off_g;
     __syncthreads();
     for (int j = threadIdx.y; j < 32; j += blockDim.y) {
       const int x = x0 + threadIdx.x, y = y0 + j;
@@ -159,19 +169,13 @@ __global__ void __launch_bounds__(256) k_transpose_x(const Box *__restrict__ box
 void launch_transpose_x(const DevState &s, const void *src, void *dst, int planes, int esize,
                         cudaStream_t st) {
   dim3 block(32, 8);
-  // grid.z = boxes x planes, at most 65535 per launch
-  const int per = (int)std::max<long long>(1, 65535 / std::max(1, s.nboxes));
-  for (int p0 = 0; p0 < planes; p0 += per) {
-    const int np = std::min(per, planes - p0);
-    dim3 grid(64, 1, (unsigned)((long long)s.nboxes * np));
-    const size_t off = (size_t)p0 * s.nghost;
-    if (esize == 8)
-      k_transpose_x<double><<<grid, block, 0, st>>>(s.boxes, s.nboxes, s.nghost,
-                                                    (const double *)src + off, (double *)dst + off, np);
-    else
-      k_transpose_x<float><<<grid, block, 0, st>>>(s.boxes, s.nboxes, s.nghost,
-                                                   (const float *)src + off, (float *)dst + off, np);
-  }
+  const int grid = 152 * 8;
+  if (esize == 8)
+    k_transpose_x<double><<<grid, block, 0, st>>>(s.boxes, s.nboxes, s.xt_tiles, s.nghost,
+                                                  (const double *)src, (double *)dst, planes);
+  else
+    k_transpose_x<float><<<grid, block, 0, st>>>(s.boxes, s.nboxes, s.xt_tiles, s.nghost,
+                                                 (const float *)src, (float *)dst, planes);
 }
 
 void launch_fine_chain(const DevState &s, const double *Uin, double *Uout, const FineChain &fc,

@@ -93,7 +93,7 @@ smc_status fill_mechanism(const smc_mechanism *mech, Mech &M, Reaction *rx) {
   M.inv_T_ref_f = (float)M.inv_T_ref;
   M.eta_exp_f = (float)M.eta_exp;
   M.inv_Pr_f = (float)M.inv_Pr;
-  for (int j = 0; j < 64; ++j) M.exp2tab[j] = (double)exp2l((long double)j / 64.0L);
+  for (int j = 0; j < 256; ++j) M.exp2tab[j] = (double)exp2l((long double)j / 256.0L);
   for (int r = 0; r < nr; ++r) {
     Reaction &R = rx[r];
     memset(&R, 0, sizeof(R));
@@ -110,6 +110,7 @@ smc_status fill_mechanism(const smc_mechanism *mech, Mech &M, Reaction *rx) {
         if (R.nf == SMC_MAX_SIDE) return SMC_ERR_ARG;
         R.fk[R.nf] = k;
         R.fcd[R.nf] = f;
+        R.fcw[R.nf] = f * mech->W[k];
         R.fc[R.nf++] = f;
         mf += f;
       }
@@ -117,6 +118,7 @@ smc_status fill_mechanism(const smc_mechanism *mech, Mech &M, Reaction *rx) {
         if (R.nr_ == SMC_MAX_SIDE) return SMC_ERR_ARG;
         R.rk[R.nr_] = k;
         R.rcd[R.nr_] = p;
+        R.rcw[R.nr_] = p * mech->W[k];
         R.rc[R.nr_++] = p;
         mr += p;
       }

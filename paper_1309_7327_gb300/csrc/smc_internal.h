@@ -33,7 +33,7 @@ struct Mech {
                                   //   : {a6, a1 - a7, -a1, -a2/2, -a3/6, -a4/12, -a5/20}
   double eta_ref, inv_T_ref, eta_exp, inv_Pr;
   double inv_ns;
-  double exp2tab[64];             // 2^(j/64), j = 0..63 (table of fast_exp)
+  double exp2tab[256];            // 2^(j/256), j = 0..255 (table of fast_exp)
   // float copies for the mixed-precision transport (no conversions in kernels)
   float hTf[SMC_MAX_NS][6];
   float Ru_Wf[SMC_MAX_NS];
@@ -46,6 +46,8 @@ struct Reaction {
   double dnu;                     // sum_k nu''_k - nu'_k
   double fcd[SMC_MAX_SIDE];       // coefficients as doubles (no int->double
   double rcd[SMC_MAX_SIDE];       //   conversions on the FP64 pipe)
+  double fcw[SMC_MAX_SIDE];       // nu' W_k and nu'' W_k: production rates in g/(cm^3 s)
+  double rcw[SMC_MAX_SIDE];       //   accumulate without a final multiply
   int nf, nr_;                    // species on each side
   int fk[SMC_MAX_SIDE], fc[SMC_MAX_SIDE];
   int rk[SMC_MAX_SIDE], rc[SMC_MAX_SIDE];
@@ -123,6 +125,7 @@ struct DevState {
   double *Q;                      // [nq][nghost]
   double *G;                      // [9][nghost] velocity gradients D_e u_c
   double *Qt, *Gt;                // the same fields with x the slowest index in each box
+  const long long *xt_tiles;      // [nboxes + 1] prefix of 32x32 (x, y) tiles per box
   double *divacc;                 // [ncells] sum_k narrow species divergence
   unsigned *status;
   Opts opt;

@@ -26,10 +26,11 @@ STATUS_NAMES = {0: "SMC_OK", 1: "SMC_ERR_ARG", 2: "SMC_ERR_CUDA", 3: "SMC_ERR_OO
                 7: "SMC_ERR_STATE"}
 
 OPT = dict(precision=0, m47=1, m48=2, diffusion_mode=3, ref_species=4, xi_ratio=5,
-           newton_tol=6, newton_maxit=7, t_guess=8, reactions=9, segment=10, profile=11)
+           newton_tol=6, newton_maxit=7, t_guess=8, reactions=9, segment=10, profile=11,
+           use_graphs=12, x_layout=13)
 KERNELS = ["prim", "grad", "march", "final", "update", "fine", "chem", "other"]
 
-EXPORTS = ["smc_create", "smc_destroy", "smc_rhs", "smc_sdc_step", "smc_prim_to_cons",
+EXPORTS = ["smc_create", "smc_destroy", "smc_rhs", "smc_sdc_step", "smc_prim_to_cons", "smc_autotune",
            "smc_set_stream", "smc_set_option", "smc_get_stats", "smc_synchronize",
            "smc_invalidate", "smc_collocation", "smc_multirate_collocation", "smc_rhs_noalloc",
            "smc_last_error"]
@@ -78,6 +79,7 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
     lib.smc_get_stats.argtypes = [vp, C.POINTER(smc_stats)]
     lib.smc_synchronize.argtypes = [vp]
     lib.smc_invalidate.argtypes = [vp]
+    lib.smc_autotune.argtypes = [vp, vp, C.POINTER(C.c_int), C.POINTER(C.c_int)]
     lib.smc_collocation.argtypes = [C.c_int, vp, vp]
     lib.smc_multirate_collocation.argtypes = [C.c_int, C.c_int, vp, vp, vp, vp]
     lib.smc_rhs_noalloc.argtypes = [C.POINTER(C.c_int), C.POINTER(C.c_double),
@@ -262,6 +264,12 @@ class Smc:
     def prim_to_cons(self, prim, out):
         self._check(lib().smc_prim_to_cons(self.h, _ptr(prim), _ptr(out)))
         return out
+
+    def autotune(self, U) -> dict:
+        """Pick the fastest stencil segment length and x-line layout at U."""
+        seg, xl = C.c_int(), C.c_int()
+        self._check(lib().smc_autotune(self.h, _ptr(U), C.byref(seg), C.byref(xl)))
+        return {"segment": seg.value, "x_layout": xl.value}
 
     def synchronize(self):
         self._check(lib().smc_synchronize(self.h))

@@ -198,3 +198,23 @@ def test_bad_arguments(smc):
             h.sdc_step(dev(U), -1.0)
         with pytest.raises(smc.SmcError):
             h.set_option("diffusion_mode", 3)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_tile_choices_give_identical_results_and_autotune(smc, precision):
+    """Segment length and x-line layout change only the schedule: every
+    choice gives the same bits; the autotuner picks one of them."""
+    wl, U, U_g = state("c1", seed=7, p_amp=0.03)
+    outs = []
+    for seg in (8, 16, 64):
+        for xl in (0, 1):
+            outs.append(gpu_rhs(smc, wl, U, precision=precision, segment=seg, x_layout=xl))
+    for o in outs[1:]:
+        assert np.array_equal(o, outs[0])
+    with smc.Smc(wl.grid, wl.mech, {"precision": precision}) as h:
+        choice = h.autotune(dev(U))
+        assert choice["segment"] in (8, 16, 32, 64) and choice["x_layout"] in (0, 1)
+        F = torch.empty_like(dev(U))
+        h.rhs(dev(U), F)
+        h.synchronize()
+    assert np.array_equal(F.cpu().numpy(), outs[0])
