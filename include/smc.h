@@ -119,7 +119,8 @@ enum {
   SMC_OPT_SEGMENT = 10,        /* cells per thread along a stencil line (default 16) */
   SMC_OPT_PROFILE = 11,        /* 1: time every kernel launch with CUDA events (default 0) */
   SMC_OPT_USE_GRAPHS = 12,     /* 1 (default): replay recycled steps as one CUDA graph when the
-                                  handle has a non-default stream; 0: launch kernels one by one */
+                                  handle has a non-default stream and profiling is off; 0: launch
+                                  kernels one by one */
   SMC_OPT_X_LAYOUT = 13        /* x-direction lines of the current precision: 0 read the box
                                   layout, 1 read an x-slowest copy (default 0 FP64, 1 mixed) */
 };

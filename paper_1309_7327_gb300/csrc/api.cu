@@ -138,6 +138,8 @@ void collect_times(smc_handle *h) {
     float ms = 0.f;
     if (cudaEventElapsedTime(&ms, p.second.first, p.second.second) == cudaSuccess)
       h->kernel_ms[p.first] += ms;
+    else
+      cudaGetLastError();   // do not leave the failure as the runtime's last error
     h->ev_free.push_back(p.second.first);
     h->ev_free.push_back(p.second.second);
   }
@@ -923,15 +925,6 @@ smc_status graph_step(smc_handle *h, double *Ud, const void *key, double dt, int
   h->n_rhs += h->graph_d_rhs;
   h->n_react += h->graph_d_react;
   for (int i = 0; i < SMC_NKERNELS; ++i) h->launches[i] += h->graph_d_launch[i];
-  if (h->profile && !h->graph_events.empty()) {
-    // the graph's events are overwritten by the next replay: read them now
-    CUDA_TRY(h, cudaStreamSynchronize(h->stream));
-    for (auto &p : h->graph_events) {
-      float ms = 0.f;
-      if (cudaEventElapsedTime(&ms, p.second.first, p.second.second) == cudaSuccess)
-        h->kernel_ms[p.first] += ms;
-    }
-  }
   return SMC_OK;
 }
 
@@ -960,7 +953,8 @@ smc_status smc_sdc_step(smc_handle *h, double *U, double dt, int nodes, int swee
   // the recycled f(U_0) is keyed by the caller's pointer (host or device)
   const bool recycled = h->cache_U == (const double *)U && h->cache_f == 0 &&
                         h->cache_kind == (reaction_substeps <= 1 ? 1 : 2);
-  if (recycled && h->use_graphs && h->stream != 0)
+  // profiling times every launch with its own events: launch eagerly then
+  if (recycled && h->use_graphs && h->stream != 0 && !h->profile)
     st = graph_step(h, Ud, U, dt, nodes, sweeps, reaction_substeps);
   else
     st = step_body(h, Ud, U, dt, nodes, sweeps, reaction_substeps);
