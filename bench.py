@@ -42,12 +42,14 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="smc", choices=["smc", "reference"])
     ap.add_argument("--workload", default="c4")
-    ap.add_argument("--precision", default="both", choices=["fp64", "mixed", "both"],
+    ap.add_argument("--precision", default="both", choices=["fp64", "mixed", "mixed_rates32", "both"],
                     help="both: the mixed path is the headline, FP64 measured beside it")
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--n", type=int, default=None,
                     help="smaller instance of the workload (profiling captures)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
+    ap.add_argument("--tiles", default=None,
+                    help="segment,x_layout,march: use this stencil schedule instead of autotuning")
     return ap.parse_args()
 
 
@@ -161,14 +163,26 @@ def chem_flops_per_eval(ns: int, nr: int, mol_sides: float = 4.0) -> float:
     return 43.0 * nr + 49.0 * ns + 31.0
 
 
-def fine_flops_per_substep(ns: int, nr: int, M1: int, Y: int) -> float:
-    """One fine substep of the multirate chain per cell: the reaction
-    evaluation, the temperature Newton solve (mixture-polynomial setup
-    13 ns, ~5 iterations of 22) and the update of eq. mrupdate
-    (NV (2 + 2 (M1 + 1)) + ns (2 + 2 Y))."""
+def fine_flops_per_substep(ns: int, nr: int, M1: int, Y: int, rates32: bool = False) -> float:
+    """FP64 flops of one fine substep of the multirate chain per cell: the
+    reaction evaluation, the temperature Newton solve (mixture-polynomial
+    setup 13 ns, ~5 iterations of 22) and the update of eq. mrupdate
+    (NV (2 + 2 (M1 + 1)) + ns (2 + 2 Y)).  With FP32-mantissa rates only their
+    FP64 part counts: per reaction the exponent (8) and the argument
+    reduction (5), per species the Gibbs energy (23) and its reduction (7)."""
     nv = 5 + ns
-    return (chem_flops_per_eval(ns, nr) + 13.0 * ns + 5 * 22 + 12
+    chem = (13.0 * nr + 30.0 * ns + 31.0) if rates32 else chem_flops_per_eval(ns, nr)
+    return (chem + 13.0 * ns + 5 * 22 + 12
             + nv * (2 + 2 * (M1 + 1)) + ns * (2 + 2 * Y))
+
+
+PRECISION_TEXT = {
+    "fp64": "fp64",
+    "mixed": ("mixed: FP32 stencil, flux and transport arithmetic; FP64 temperature, Gibbs "
+              "energies, exponentials, rates and SDC accumulation"),
+    "mixed_rates32": ("mixed with FP32-mantissa rates: as mixed, but the exponentials after their "
+                      "FP64 argument reduction, the concentration products and the rate sums in FP32"),
+}
 
 
 def measured_peaks():
@@ -262,9 +276,14 @@ def main():
     ncells = wl.grid.ncells
     nv = 5 + wl.mech.ns
 
-    def measure(precision: int):
+    variants = {"fp64": {"precision": 0}, "mixed": {"precision": 1},
+                "mixed_rates32": {"precision": 1, "rates": 1}}
+
+    def measure(name: str):
         """Warm up, then time args.steps steps on device-resident state."""
-        h = smc.Smc(wl.grid, wl.mech, {"precision": precision})
+        opts = variants[name]
+        precision = opts["precision"]
+        h = smc.Smc(wl.grid, wl.mech, opts)
         stream = torch.cuda.Stream(device)
         h.set_stream(stream)
         prim = torch.from_numpy(wl.prim).to(device)
@@ -274,7 +293,14 @@ def main():
         h.synchronize()
         del prim
         U0 = U.clone()
-        tuned = h.autotune(U)                 # segment length and x-line layout
+        if args.tiles:                        # a fixed schedule (profiling runs)
+            seg, xl, mv = (int(v) for v in args.tiles.split(","))
+            h.set_option("segment", seg)
+            h.set_option("x_layout", xl)
+            h.set_option("march", mv if precision == 1 else 0)
+            tuned = {"segment": seg, "x_layout": xl, "march": mv if precision == 1 else 0}
+        else:
+            tuned = h.autotune(U)             # segment length, x-line layout, line kernel
         for _ in range(args.warmup):          # also fills the recycled f(U_0)
             h.sdc_step(U, wl.dt, nodes, sweeps, rsub)
         h.synchronize()
@@ -309,15 +335,14 @@ def main():
                     clocks=clocks, U0=U0, tuned=tuned)
 
     runs = {}
-    if args.precision in ("mixed", "both"):
-        runs["mixed"] = measure(1)
-    if args.precision in ("fp64", "both"):
-        runs["fp64"] = measure(0)
-    main_key = "mixed" if "mixed" in runs else "fp64"
+    order = {"both": ["mixed", "fp64", "mixed_rates32"]}.get(args.precision, [args.precision])
+    for name in order:
+        runs[name] = measure(name)
+    main_key = order[0]
     R = runs[main_key]
     ms_step, launches, kms, clocks, U0 = R["ms_step"], R["launches"], R["kms"], R["clocks"], R["U0"]
     value = world * ncells * evals_per_step / (ms_step / 1e3) / 1e6
-    mixed_prec = 1 if main_key == "mixed" else 0
+    main_opts = variants[main_key]
 
     # rooflines of the two heaviest kernels; "roofline" is the one with the
     # larger share of the step
@@ -333,7 +358,7 @@ def main():
     n_march = launches["march"]
     if n_march:
         march_ms = kms["march"] / n_march
-        if main_key == "fp64":
+        if main_opts["precision"] == 0:
             fl, peak, src = march_flops_per_cell(wl.mech.ns) * ncells, fp64_peak, "FP64 pipe"
         else:
             fl, peak, src = march_flops_per_cell_mixed(wl.mech.ns) * ncells, fp32_peak, "FP32 pipe"
@@ -348,7 +373,8 @@ def main():
     if n_fine:
         per = rsub - 1
         fine_ms = kms["fine"] / n_fine
-        fl = fine_flops_per_substep(wl.mech.ns, wl.mech.nr, M1, rsub) * ncells * per
+        fl = fine_flops_per_substep(wl.mech.ns, wl.mech.nr, M1, rsub,
+                                    rates32=main_opts.get("rates", 0) == 1) * ncells * per
         rooflines["k_fine_chain"] = {
             "bound": "alu", "kernel": "k_fine_chain (reaction substeps of one coarse interval)",
             "achieved": fl / (fine_ms / 1e3) / 1e12, "peak": fp64_peak / 1e12, "unit": "TFLOP/s",
@@ -376,11 +402,15 @@ def main():
                         for k, r in runs.items()}
     if "mixed" in runs and "fp64" in runs:
         precision_report["mixed_speedup_vs_fp64"] = runs["fp64"]["ms_step"] / runs["mixed"]["ms_step"]
+    if "mixed_rates32" in runs and "fp64" in runs:
+        precision_report["mixed_rates32_speedup_vs_fp64"] = (runs["fp64"]["ms_step"]
+                                                             / runs["mixed_rates32"]["ms_step"])
 
     # end to end: host buffers through the C ABI, copies inside the timed region
     Uh = U0.cpu().numpy().copy()
-    h2 = smc.Smc(wl.grid, wl.mech, {"precision": mixed_prec, "segment": R["tuned"]["segment"],
-                                    "x_layout": R["tuned"]["x_layout"]})
+    h2 = smc.Smc(wl.grid, wl.mech, dict(main_opts, segment=R["tuned"]["segment"],
+                                        x_layout=R["tuned"]["x_layout"],
+                                        march=R["tuned"]["march"]))
     h2.sdc_step(Uh, wl.dt, nodes, sweeps, rsub)
     e2e_steps = max(1, min(args.steps, 3))
     t0 = time.perf_counter()
@@ -398,7 +428,7 @@ def main():
             "metric": "Mcell-RHS/s (21 species)", "value": value, "unit": "Mcell-RHS/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32+f64" if main_key == "mixed" else "f64",
+            "dtype": "f64" if main_key == "fp64" else "f32+f64",
             "data": "synthetic",
             "config": {"workload": args.workload + (f" (n={args.n})" if args.n else ""), "boxes": wl.grid.nboxes, "cells": ncells,
                        "species": wl.mech.ns, "reactions": wl.mech.nr,
@@ -406,8 +436,7 @@ def main():
                                       if rsub >= 2 else f"SDC {nodes} GL, {sweeps} sweeps"),
                        "rhs_evals_per_step": evals_per_step,
                        "reaction_evals_per_step": sweeps * M1 * per if per else 0,
-                       "precision": ("mixed: FP32 stencils/transport, FP64 T, Gibbs, exp, "
-                                     "rates, SDC accumulation") if main_key == "mixed" else "fp64",
+                       "precision": PRECISION_TEXT[main_key],
                        "l2": "inputs larger than L2 (state %.0f MB)" % (nv * ncells * 8 / 1e6),
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "roofline": roofline, "rooflines": rooflines, "hbm": hbm, "cpu_baseline": cpu, "e2e": e2e,

@@ -106,7 +106,9 @@ typedef struct { int lo[3], hi[3]; } smc_bc;
 
 /* Options for smc_set_option (value given as a double). */
 enum {
-  SMC_OPT_PRECISION = 0,       /* 0: FP64 everywhere (default); 1: mixed */
+  SMC_OPT_PRECISION = 0,       /* 0: FP64 everywhere (default); 1: mixed -- FP32 stencil, flux
+                                  and transport arithmetic on float pairs, FP64 temperature,
+                                  Gibbs energies, exponentials, rates and all accumulation */
   SMC_OPT_M47 = 1,             /* free parameters of the 8th-order narrow */
   SMC_OPT_M48 = 2,             /* stencil (Sec. 2.2); default 3557/44100, -2083/117600 */
   SMC_OPT_DIFFUSION_MODE = 3,  /* 0: correction velocity (default, Sec. 2.4); 1: reference species */
@@ -121,8 +123,20 @@ enum {
   SMC_OPT_USE_GRAPHS = 12,     /* 1 (default): replay recycled steps as one CUDA graph when the
                                   handle has a non-default stream and profiling is off; 0: launch
                                   kernels one by one */
-  SMC_OPT_X_LAYOUT = 13        /* x-direction lines of the current precision: 0 read the box
+  SMC_OPT_X_LAYOUT = 13,       /* x-direction lines of the current precision: 0 read the box
                                   layout, 1 read an x-slowest copy (default 0 FP64, 1 mixed) */
+  SMC_OPT_MARCH = 14,          /* stencil-line kernel of the current precision: 0 evaluates
+                                  every face from its 8-point window, 1 slides 9-cell register
+                                  windows along the line, one load per field and cell
+                                  (mixed only; default 0 FP64, 1 mixed) */
+  SMC_OPT_RATES = 15,          /* production rates under SMC_OPT_PRECISION = 1: 0 (default)
+                                  FP64 like the FP64 path; 1 FP32 mantissas after FP64 Gibbs
+                                  energies, reaction exponents and exponent reductions
+                                  (about 1e-6 relative; ignored in FP64 precision) */
+  SMC_OPT_FINE_REPEAT = 16     /* multirate fine nodes (Sec. 3.2): each coarse interval holds
+                                  this many consecutive groups of reaction_substeps
+                                  Gauss-Lobatto nodes; 1 (default) is type (b), more is
+                                  type (c) (1..8; at most 64 fine intervals per step) */
 };
 
 /* Kernel classes counted in smc_stats (launches always; times only while
@@ -203,23 +217,27 @@ smc_status smc_invalidate(smc_handle *h);
 
 /* Autotune the stencil kernels for the handle's current precision: time
  * one right-hand-side evaluation at U (device memory, box layout) for every
- * segment length (cells per thread along a stencil line: 8, 16, 32, 64) and
+ * segment length (cells per thread along a stencil line: 8, 16, 32, 64),
  * both layouts of the x-direction lines (0: read the box layout directly;
- * 1: read a copy with x the slowest index, made once per evaluation), and
- * keep the fastest.  *segment and *x_layout (may be NULL) receive the choice.
- * Synchronises the handle's stream. */
-smc_status smc_autotune(smc_handle *h, const double *U, int *segment, int *x_layout);
+ * 1: read a copy with x the slowest index, made once per evaluation) and
+ * every stencil-line kernel of the precision (SMC_OPT_MARCH), and keep the
+ * fastest.  *segment, *x_layout and *march (each may be NULL) receive the
+ * choice.  Synchronises the handle's stream. */
+smc_status smc_autotune(smc_handle *h, const double *U, int *segment, int *x_layout, int *march);
 
 /* Collocation data used by smc_sdc_step (host computation, no GPU needed).
  * smc_collocation: the `nodes` Gauss-Lobatto nodes on [0, 1] (tau[nodes])
  * and the node-to-node integration matrix S[(nodes-1) * nodes] of Sec. 3.1,
  * s_mj = integral over [tau_m, tau_{m+1}] of the Lagrange polynomial L_j.
- * smc_multirate_collocation: coarse nodes t1[coarse], fine nodes
- * t2[M2 + 1] (M2 = (coarse-1)(fine-1), type (b) of Sec. 3.2), and the
- * matrices S21[M2 * coarse] and S22[M2 * (M2 + 1)] of eq. mrupdate, per unit
- * time step.  All arrays are caller-owned host memory. */
+ * smc_multirate_collocation: coarse nodes t1[coarse] and fine nodes
+ * t2[M2 + 1] of Sec. 3.2 -- `repeat` consecutive groups of `fine`
+ * Gauss-Lobatto nodes in every coarse interval (type (b) for repeat = 1,
+ * type (c) otherwise), M2 = (coarse-1)(fine-1) repeat -- and the matrices
+ * S21[M2 * coarse] (coarse Lagrange basis) and S22[M2 * (M2 + 1)] (the
+ * piecewise basis of each group) of eq. mrupdate, per unit time step.  All
+ * arrays are caller-owned host memory. */
 smc_status smc_collocation(int nodes, double *tau, double *S);
-smc_status smc_multirate_collocation(int coarse, int fine, double *t1, double *t2,
+smc_status smc_multirate_collocation(int coarse, int fine, int repeat, double *t1, double *t2,
                                      double *S21, double *S22);
 
 /* The FP64 right-hand side of smc_rhs for ONE triply periodic box of
@@ -242,6 +260,14 @@ smc_status smc_multirate_collocation(int coarse, int fine, double *t1, double *t
  * the GPU race and must be serialised by the caller. */
 smc_status smc_rhs_noalloc(const int n[3], const double dx[3], const smc_mechanism *mech,
                            const double *U, double *dUdt, void *stream);
+
+/* The exponential used by the production rates (a table-driven method, not
+ * the paper's: Sec. 2.1 only needs exp), applied elementwise y[i] = exp(x[i])
+ * on the device for accuracy tests.  x and y are caller-owned device arrays
+ * of n doubles (n >= 0).  Arguments with |x| >= 512 are clamped to
+ * [-708, 709].  Synchronous; returns SMC_ERR_ARG for null arrays or
+ * host pointers, SMC_ERR_CUDA if the launch fails. */
+smc_status smc_exp(const double *x, double *y, long long n);
 
 /* Message describing the last error on this handle ("" if none).  The
  * string is owned by the handle. */

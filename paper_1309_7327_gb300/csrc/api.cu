@@ -25,6 +25,9 @@ struct smc_handle {
   int precision = 0;
   int segment = 16;
   int xt[2] = {0, 1};                   // x lines on the x-slowest copy (FP64, mixed)
+  int march[2] = {0, 1};                // stencil-line kernel (FP64, mixed)
+  int rates32 = 0;                      // FP32-mantissa production rates (mixed only)
+  int fine_repeat = 1;                  // groups of fine nodes per coarse interval (type (c) if > 1)
   cudaStream_t stream = 0;
   int device = 0;
 
@@ -172,6 +175,7 @@ DevState state(smc_handle *h) {
   s.divacc = h->d_divacc;
   s.status = h->d_status;
   s.opt = h->opt;
+  s.opt.rates32 = h->rates32 && h->precision == 1;
   s.xi_ratio_f = (float)h->opt.xi_ratio;
   return s;
 }
@@ -375,7 +379,8 @@ smc_status eval_rhs(smc_handle *h, const double *U, double *F, int transport, in
     }
     for (int d = 0; d < 3; ++d) {
       Timed t(h, SMC_K_MARCH);
-      if (mixed) launch_march_m(d == 0 ? sx : s, d, h->d_dUf, d == 0, h->stream);
+      if (mixed && h->march[1]) launch_march_m2(d == 0 ? sx : s, d, h->d_dUf, d == 0, h->stream);
+      else if (mixed) launch_march_m(d == 0 ? sx : s, d, h->d_dUf, d == 0, h->stream);
       else launch_march(d == 0 ? sx : s, d, F, d == 0, h->stream);
     }
   }
@@ -458,10 +463,11 @@ smc_status sdc_single_rate(smc_handle *h, double *U, const void *key, double dt,
 
 smc_status sdc_multirate(smc_handle *h, double *U, const void *key, double dt, int coarse, int sweeps,
                          int fine) {
-  const int M1 = coarse - 1, per = fine - 1, M2 = M1 * per;
-  if (M1 > 4 || per > 8 || M2 > 32) return fail(h, SMC_ERR_ARG, "too many multirate nodes");
+  const int repeat = h->fine_repeat;
+  const int M1 = coarse - 1, sub = fine - 1, per = sub * repeat, M2 = M1 * per;
+  if (M1 > 4 || sub > 8 || M2 > 64) return fail(h, SMC_ERR_ARG, "too many multirate nodes");
   std::vector<double> t1, t2, S21, S22;
-  multirate_matrices(coarse, fine, t1, t2, S21, S22);
+  multirate_matrices(coarse, fine, repeat, t1, t2, S21, S22);
   smc_status st = ensure_pools(h, 2 * M1 + 1, 2 * M2 + 1);
   if (st) return st;
   const long long n = (long long)h->nv * h->ncells;
@@ -498,29 +504,38 @@ smc_status sdc_multirate(smc_handle *h, double *U, const void *key, double dt, i
         if (st) return st;
         h->n_rhs++;
       }
-      FineChain fc;
-      memset(&fc, 0, sizeof(fc));
-      fc.q0 = p * per;
-      fc.nsub = per;
-      fc.p = p;
-      fc.M1 = M1;
-      for (int sidx = 0; sidx < per; ++sidx) {
-        const int q = fc.q0 + sidx;
-        fc.dtq[sidx] = dt * (t2[q + 1] - t2[q]);
-        for (int j = 0; j <= M1; ++j) fc.s21[sidx][j] = dt * S21[q * (M1 + 1) + j];
-        for (int t = 0; t <= per; ++t) fc.s22[sidx][t] = dt * S22[q * (M2 + 1) + fc.q0 + t];
+      // one chain per group of `fine` nodes (one group per coarse interval
+      // for type (b), `repeat` groups for type (c)); S22 couples only the
+      // nodes of a group
+      for (int r = 0; r < repeat; ++r) {
+        FineChain fc;
+        memset(&fc, 0, sizeof(fc));
+        fc.q0 = p * per + r * sub;
+        fc.nsub = sub;
+        fc.p = p;
+        fc.M1 = M1;
+        for (int sidx = 0; sidx < sub; ++sidx) {
+          const int q = fc.q0 + sidx;
+          fc.dtq[sidx] = dt * (t2[q + 1] - t2[q]);
+          for (int j = 0; j <= M1; ++j) fc.s21[sidx][j] = dt * S21[q * (M1 + 1) + j];
+          for (int t = 0; t <= sub; ++t) fc.s22[sidx][t] = dt * S22[q * (M2 + 1) + fc.q0 + t];
+          // dtq [f(new) - f(old)] with f(old) one of the quadrature's own
+          // nodes: fold -dtq into that node's weight
+          fc.s21[sidx][p] -= fc.dtq[sidx];
+          fc.s22[sidx][sidx] -= fc.dtq[sidx];
+        }
+        fc.F1new_p = h->fpool[f1new[p]];
+        for (int j = 0; j <= M1; ++j) fc.F1old[j] = h->fpool[f1old[j]];
+        for (int t = 0; t <= sub; ++t) {
+          fc.F2old[t] = h->rpool[f2old[fc.q0 + t]];
+          fc.F2new[t] = h->rpool[f2new[fc.q0 + t]];
+        }
+        fc.eval_first = fc.q0 > 0;
+        fc.eval_last = (p == M1 - 1 && r == repeat - 1);
+        const bool first = p == 0 && r == 0;
+        { Timed t(h, SMC_K_FINE); launch_fine_chain(s, first ? h->d_U0 : U, U, fc, h->stream); }
+        h->n_react += sub - (fc.eval_first ? 0 : 1) + (fc.eval_last ? 1 : 0);
       }
-      fc.F1new_p = h->fpool[f1new[p]];
-      fc.F1old_p = h->fpool[f1old[p]];
-      for (int j = 0; j <= M1; ++j) fc.F1old[j] = h->fpool[f1old[j]];
-      for (int t = 0; t <= per; ++t) {
-        fc.F2old[t] = h->rpool[f2old[fc.q0 + t]];
-        fc.F2new[t] = h->rpool[f2new[fc.q0 + t]];
-      }
-      fc.eval_first = fc.q0 > 0;
-      fc.eval_last = (p == M1 - 1);
-      { Timed t(h, SMC_K_FINE); launch_fine_chain(s, p == 0 ? h->d_U0 : U, U, fc, h->stream); }
-      h->n_react += per - (fc.eval_first ? 0 : 1) + (fc.eval_last ? 1 : 0);
     }
     st = eval_rhs(h, U, h->fpool[f1new[M1]], 1, 0);
     if (st) return st;
@@ -565,121 +580,12 @@ smc_status smc_create(const smc_grid *grid, const smc_mechanism *mech, const smc
         return bail(fail(h, SMC_ERR_ARG, "only periodic boundaries are supported"));
   }
   // ---- mechanism
+  if (const char *why = pack_mechanism(mech, 1024, h->hmech, h->hrx))
+    return bail(fail(h, SMC_ERR_ARG, why));
   const int ns = mech->nspecies, nr = mech->nreactions;
-  if (ns < 1 || ns > SMC_MAX_NS) return bail(fail(h, SMC_ERR_ARG, "nspecies must be 1..64"));
-  if (nr < 0 || nr > 1024) return bail(fail(h, SMC_ERR_ARG, "nreactions must be 0..1024"));
-  if (!mech->W || !mech->nasa7 || !mech->Le || (nr > 0 && (!mech->nu_f || !mech->nu_r || !mech->A ||
-                                                           !mech->b || !mech->Ea)))
-    return bail(fail(h, SMC_ERR_ARG, "null mechanism array"));
   h->ns = ns;
   h->nv = 5 + ns;
   h->nr = nr;
-  Mech &M = h->hmech;
-  memset(&M, 0, sizeof(M));
-  M.ns = ns;
-  M.nr = nr;
-  for (int k = 0; k < ns; ++k) {
-    const double W = mech->W[k];
-    if (!(W > 0) || !(mech->Le[k] > 0)) return bail(fail(h, SMC_ERR_ARG, "W and Le must be positive"));
-    const double *a = mech->nasa7 + 7 * k;
-    M.W[k] = W;
-    M.invW[k] = 1.0 / W;
-    M.Ru_W[k] = kRu / W;
-    M.invLe[k] = 1.0 / mech->Le[k];
-    for (int i = 0; i < 5; ++i) M.cp[k][i] = a[i];
-    M.hT[k][0] = a[5];
-    M.hT[k][1] = a[0];
-    M.hT[k][2] = a[1] / 2;
-    M.hT[k][3] = a[2] / 3;
-    M.hT[k][4] = a[3] / 4;
-    M.hT[k][5] = a[4] / 5;
-    M.sR[k][0] = a[0];
-    M.sR[k][1] = a[6];
-    M.sR[k][2] = a[1];
-    M.sR[k][3] = a[2] / 2;
-    M.sR[k][4] = a[3] / 3;
-    M.sR[k][5] = a[4] / 4;
-    {
-      const double gR[7] = {a[5], a[0] - a[6], -a[0], -a[1] / 2, -a[2] / 6, -a[3] / 12, -a[4] / 20};
-      for (int i = 0; i < 7; ++i) M.gR[k][i] = gR[i];
-    }
-    for (int i = 0; i <= 100; ++i) {
-      const double T = 200.0 + 33.0 * i;
-      const double cp = a[0] + T * (a[1] + T * (a[2] + T * (a[3] + T * a[4])));
-      if (!(cp > 0)) return bail(fail(h, SMC_ERR_ARG, "cp must be positive on 200..3500 K"));
-    }
-  }
-  if (!(mech->eta_ref > 0) || !(mech->T_ref > 0) || !(mech->Pr > 0))
-    return bail(fail(h, SMC_ERR_ARG, "transport parameters must be positive"));
-  M.inv_ns = 1.0 / ns;
-  for (int j = 0; j < 256; ++j) M.exp2tab[j] = (double)exp2l((long double)j / 256.0L);
-  for (int i = 0; i <= 100; ++i) {
-    // the production-rate evaluation needs the species' g/RT to spread over
-    // less than 400 (see production_rates)
-    const double T = 200.0 + 33.0 * i, lnT = log(T);
-    double gmin = 1e300, gmax = -1e300;
-    for (int k = 0; k < ns; ++k) {
-      const double *a = mech->nasa7 + 7 * k;
-      const double hRT = a[0] + T * (a[1] / 2 + T * (a[2] / 3 + T * (a[3] / 4 + T * a[4] / 5))) + a[5] / T;
-      const double sR = a[0] * lnT + T * (a[1] + T * (a[2] / 2 + T * (a[3] / 3 + T * a[4] / 4))) + a[6];
-      gmin = std::min(gmin, hRT - sR);
-      gmax = std::max(gmax, hRT - sR);
-    }
-    if (!(gmax - gmin < 400.0))
-      return bail(fail(h, SMC_ERR_ARG, "species Gibbs energies g/RT spread over more than 400"));
-  }
-  M.eta_ref = mech->eta_ref;
-  M.inv_T_ref = 1.0 / mech->T_ref;
-  M.eta_exp = mech->eta_exp;
-  M.inv_Pr = 1.0 / mech->Pr;
-  for (int k = 0; k < ns; ++k) {
-    for (int i = 0; i < 6; ++i) M.hTf[k][i] = (float)M.hT[k][i];
-    M.Ru_Wf[k] = (float)M.Ru_W[k];
-    M.invLef[k] = (float)M.invLe[k];
-  }
-  M.eta_ref_f = (float)M.eta_ref;
-  M.inv_T_ref_f = (float)M.inv_T_ref;
-  M.eta_exp_f = (float)M.eta_exp;
-  M.inv_Pr_f = (float)M.inv_Pr;
-  h->hrx.resize(nr);
-  for (int r = 0; r < nr; ++r) {
-    Reaction &R = h->hrx[r];
-    memset(&R, 0, sizeof(R));
-    if (!(mech->A[r] > 0)) return bail(fail(h, SMC_ERR_ARG, "A must be positive"));
-    R.lnA = log(mech->A[r]);
-    R.b = mech->b[r];
-    R.Ea_R = mech->Ea[r] / kRc;
-    double dnu = 0, mass = 0, scale = 0;
-    for (int k = 0; k < ns; ++k) {
-      const int f = mech->nu_f[r * ns + k], p = mech->nu_r[r * ns + k];
-      if (f < 0 || p < 0) return bail(fail(h, SMC_ERR_ARG, "negative stoichiometric coefficient"));
-      if (f > 0) {
-        if (R.nf == SMC_MAX_SIDE) return bail(fail(h, SMC_ERR_ARG, "more than 4 reactant species"));
-        R.fk[R.nf] = k;
-        R.fcd[R.nf] = f;
-        R.fcw[R.nf] = f * mech->W[k];
-        R.fc[R.nf++] = f;
-      }
-      if (p > 0) {
-        if (R.nr_ == SMC_MAX_SIDE) return bail(fail(h, SMC_ERR_ARG, "more than 4 product species"));
-        R.rk[R.nr_] = k;
-        R.rcd[R.nr_] = p;
-        R.rcw[R.nr_] = p * mech->W[k];
-        R.rc[R.nr_++] = p;
-      }
-      dnu += p - f;
-      mass += (p - f) * mech->W[k];
-      scale += (p + f) * mech->W[k];
-    }
-    if (R.nf == 0 || R.nr_ == 0) return bail(fail(h, SMC_ERR_ARG, "empty reaction side"));
-    if (fabs(mass) > 1e-9 * scale) return bail(fail(h, SMC_ERR_ARG, "reaction does not conserve mass"));
-    int mol_f = 0, mol_r = 0;
-    for (int i = 0; i < R.nf; ++i) mol_f += R.fc[i];
-    for (int i = 0; i < R.nr_; ++i) mol_r += R.rc[i];
-    if (mol_f > 3 || mol_r > 3) return bail(fail(h, SMC_ERR_ARG, "more than three molecules on a reaction side"));
-    R.dnu = dnu;
-    R.dn = (int)dnu;
-  }
   // ---- grid
   if (grid->nboxes < 1 || !grid->lo || !grid->hi) return bail(fail(h, SMC_ERR_ARG, "no boxes"));
   for (int d = 0; d < 3; ++d) {
@@ -1036,6 +942,20 @@ smc_status smc_set_option(smc_handle *h, int key, double v) {
       if (v != 0.0 && v != 1.0) return fail(h, SMC_ERR_ARG, "x layout must be 0 or 1");
       h->xt[h->precision == 1] = (int)v;
       return SMC_OK;
+    case SMC_OPT_MARCH:
+      if (v != 0.0 && v != 1.0) return fail(h, SMC_ERR_ARG, "march kernel must be 0 or 1");
+      if (v == 1.0 && h->precision != 1)
+        return fail(h, SMC_ERR_ARG, "the sliding-window line kernel is mixed precision only");
+      h->march[h->precision == 1] = (int)v;
+      return SMC_OK;
+    case SMC_OPT_FINE_REPEAT:
+      if (v < 1 || v > 8 || v != floor(v)) return fail(h, SMC_ERR_ARG, "fine repeat must be 1..8");
+      h->fine_repeat = (int)v;
+      return SMC_OK;
+    case SMC_OPT_RATES:
+      if (v != 0.0 && v != 1.0) return fail(h, SMC_ERR_ARG, "rates must be 0 or 1");
+      h->rates32 = (int)v;
+      return SMC_OK;
     case SMC_OPT_PROFILE:
       cudaStreamSynchronize(h->stream);
       collect_times(h);
@@ -1084,7 +1004,7 @@ smc_status smc_invalidate(smc_handle *h) {
   return SMC_OK;
 }
 
-smc_status smc_autotune(smc_handle *h, const double *U, int *segment, int *x_layout) {
+smc_status smc_autotune(smc_handle *h, const double *U, int *segment, int *x_layout, int *march) {
   if (!h || !h->d_Q) return SMC_ERR_STATE;
   if (!U || !is_device_ptr(U)) return fail(h, SMC_ERR_ARG, "autotune needs U in device memory");
   smc_status st = ensure_pools(h, 1, 0);
@@ -1092,40 +1012,45 @@ smc_status smc_autotune(smc_handle *h, const double *U, int *segment, int *x_lay
   double *F = h->fpool[0];
   h->cache_kind = 0;   // slot 0 is overwritten
   const int mixed = h->precision == 1;
-  const int seg0 = h->segment, xt0 = h->xt[mixed];
   const int segs[4] = {8, 16, 32, 64};
+  const int nvar = mixed ? 2 : 1;
   float best = 1e30f;
-  int best_seg = seg0, best_xt = xt0;
+  int best_seg = h->segment, best_xt = h->xt[mixed], best_mv = h->march[mixed];
   cudaEvent_t a, b;
   CUDA_TRY(h, cudaEventCreate(&a));
   CUDA_TRY(h, cudaEventCreate(&b));
-  for (int si = 0; si < 4; ++si)
-    for (int x = 0; x < 2; ++x) {
-      h->segment = segs[si];
-      h->xt[mixed] = x;
-      if ((st = build_lines(h))) return st;
-      if ((st = eval_rhs(h, U, F, 1, 1))) return st;      // warm-up (allocations)
-      CUDA_TRY(h, cudaEventRecord(a, h->stream));
-      for (int r = 0; r < 2; ++r)
-        if ((st = eval_rhs(h, U, F, 1, 1))) return st;
-      CUDA_TRY(h, cudaEventRecord(b, h->stream));
-      CUDA_TRY(h, cudaEventSynchronize(b));
-      float ms = 0.f;
-      CUDA_TRY(h, cudaEventElapsedTime(&ms, a, b));
-      if (ms < best) {
-        best = ms;
-        best_seg = segs[si];
-        best_xt = x;
+  for (int mv = 0; mv < nvar; ++mv)
+    for (int si = 0; si < 4; ++si)
+      for (int x = 0; x < 2; ++x) {
+        h->segment = segs[si];
+        h->xt[mixed] = x;
+        h->march[mixed] = mv;
+        if ((st = build_lines(h))) return st;
+        if ((st = eval_rhs(h, U, F, 1, 1))) return st;      // warm-up (allocations)
+        CUDA_TRY(h, cudaEventRecord(a, h->stream));
+        for (int r = 0; r < 2; ++r)
+          if ((st = eval_rhs(h, U, F, 1, 1))) return st;
+        CUDA_TRY(h, cudaEventRecord(b, h->stream));
+        CUDA_TRY(h, cudaEventSynchronize(b));
+        float ms = 0.f;
+        CUDA_TRY(h, cudaEventElapsedTime(&ms, a, b));
+        if (ms < best) {
+          best = ms;
+          best_seg = segs[si];
+          best_xt = x;
+          best_mv = mv;
+        }
       }
-    }
   cudaEventDestroy(a);
   cudaEventDestroy(b);
   h->segment = best_seg;
   h->xt[mixed] = best_xt;
+  h->march[mixed] = best_mv;
   if ((st = build_lines(h))) return st;
   h->opt_version++;
   if (segment) *segment = best_seg;
   if (x_layout) *x_layout = best_xt;
+  if (march) *march = best_mv;
   return check_flags(h);
 }
 
@@ -1139,17 +1064,41 @@ smc_status smc_collocation(int nodes, double *tau, double *S) {
   return SMC_OK;
 }
 
-smc_status smc_multirate_collocation(int coarse, int fine, double *t1, double *t2, double *S21,
-                                     double *S22) {
-  if (coarse < 2 || coarse > 9 || fine < 2 || fine > 9 || !t1 || !t2 || !S21 || !S22)
+smc_status smc_multirate_collocation(int coarse, int fine, int repeat, double *t1, double *t2,
+                                     double *S21, double *S22) {
+  if (coarse < 2 || coarse > 9 || fine < 2 || fine > 9 || repeat < 1 || repeat > 8 || !t1 || !t2 ||
+      !S21 || !S22)
     return SMC_ERR_ARG;
   std::vector<double> a, b, c, d;
-  multirate_matrices(coarse, fine, a, b, c, d);
+  multirate_matrices(coarse, fine, repeat, a, b, c, d);
   std::copy(a.begin(), a.end(), t1);
   std::copy(b.begin(), b.end(), t2);
   std::copy(c.begin(), c.end(), S21);
   std::copy(d.begin(), d.end(), S22);
   return SMC_OK;
+}
+
+smc_status smc_exp(const double *x, double *y, long long n) {
+  if (n < 0 || (n > 0 && (!x || !y))) return SMC_ERR_ARG;
+  if (n == 0) return SMC_OK;
+  if (!is_device_ptr(x) || !is_device_ptr(y)) return SMC_ERR_ARG;
+  Mech *hm = new Mech();
+  memset(hm, 0, sizeof(Mech));
+  for (int j = 0; j < SMC_EXP_TABLE; ++j)
+    hm->exp2tab[j] = (double)exp2l((long double)j / (long double)SMC_EXP_TABLE);
+  Mech *dm = nullptr;
+  smc_status st = SMC_OK;
+  if (cudaMalloc(&dm, sizeof(Mech)) != cudaSuccess) {
+    delete hm;
+    return SMC_ERR_CUDA;
+  }
+  if (cudaMemcpy(dm, hm, sizeof(Mech), cudaMemcpyHostToDevice) != cudaSuccess) st = SMC_ERR_CUDA;
+  if (!st) launch_exp(dm, x, y, n, 0);
+  if (!st && (cudaGetLastError() != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess))
+    st = SMC_ERR_CUDA;
+  cudaFree(dm);
+  delete hm;
+  return st;
 }
 
 const char *smc_last_error(smc_handle *h) {

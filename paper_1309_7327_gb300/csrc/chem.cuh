@@ -5,31 +5,48 @@
 
 namespace smc {
 
+// Truncating double -> float conversion in integer arithmetic (keeps the
+// FP64 pipe free): the top 23 stored mantissa bits are kept; magnitudes below
+// the float normal range flush to zero.  Exact when x has at most 24
+// significant bits.
+__device__ __forceinline__ float trunc_float(double x) {
+  const long long b = __double_as_longlong(x);
+  const int e = (int)((b >> 52) & 0x7ff) - 1023 + 127;
+  const unsigned sign = (unsigned)((unsigned long long)b >> 63) << 31;
+  if (e <= 0) return __uint_as_float(sign);
+  if (e >= 255) return __uint_as_float(sign | 0x7f800000u);
+  return __uint_as_float(sign | ((unsigned)e << 23) | (unsigned)((b >> 29) & 0x7fffff));
+}
+
+
 // exp(x) in FP64 by the table-driven method of P. T. P. Tang (ACM TOMS 15,
-// 1989): x = (256 k + j) ln2/256 + r with |r| <= ln2/512, so that
-//   exp(x) = 2^k * 2^(j/256) * exp(r),
-// 2^(j/256) from a 256-entry table and exp(r) - 1 from its Taylor polynomial
-// to r^4 (truncation r^5/120 < 4e-17 relative).  n = 256 k + j is rounded with
-// the 1.5 * 2^52 shift, and 2^k is applied to the exponent field with integer
+// 1989): x = (2048 k + j) ln2/2048 + r with |r| <= ln2/4096, so that
+//   exp(x) = 2^k * 2^(j/2048) * exp(r),
+// 2^(j/2048) from a 2048-entry table and exp(r) - 1 from its Taylor
+// polynomial to r^3 (truncation r^4/24 < 4e-17 relative).  n = 2048 k + j is
+// rounded with the 1.5 * 2^52 shift inside one FMA (the product x * 2048/ln2
+// is exact inside it), and 2^k is applied to the exponent field with integer
 // arithmetic.  |x| >= 512 is clamped to [-708, 709] (the normal range of the
-// result).  About 11 FP64 operations; error within ~1 ulp.
+// result).  Eight FP64 operations; error within about 1 ulp.
 __device__ __forceinline__ double fast_exp(const Mech &m, double x) {
   // clamp only when |x| >= 512 (exponent field test in integer arithmetic;
-  // NaN also takes this branch and stays NaN)
-  if ((__double2hiint(x) & 0x7ff00000) >= ((1023 + 9) << 20)) x = fmin(fmax(x, -708.0), 709.0);
+  // NaN also takes this branch and is returned as it is)
+  if ((__double2hiint(x) & 0x7ff00000) >= ((1023 + 9) << 20)) {
+    if (x != x) return x;
+    if (x > 709.0) x = 709.0;
+    if (x < -708.0) x = -708.0;
+  }
   const double shift = 6755399441055744.0;                 // 1.5 * 2^52
-  const double t = x * 369.3299304675746;                  // 256 / ln 2
-  const double nd = (t + shift) - shift;                   // nearest integer
-  const int n = __double2loint(t + shift);
-  // ln2/256 split: L1 has 19 trailing zero bits so nd * L1 is exact for |n| < 2^19
-  const double L1 = 0.002707606173999011, L2 = 6.327543041662719e-14;
+  const double u = fma(x, 2954.639443740597, shift);       // 2048 / ln 2
+  const double nd = u - shift;                             // nearest integer to x 2048/ln2
+  const int n = __double2loint(u);
+  // ln2/2048 split: L1 has 29 significant bits, so nd * L1 is exact for |n| < 2^22
+  const double L1 = 0.0003384507717782981, L2 = -2.0512280628325608e-14;
   const double r = fma(-nd, L2, fma(-nd, L1, x));
-  double q = 1.0 / 24.0;
-  q = fma(q, r, 1.0 / 6.0);
-  q = fma(q, r, 0.5);
+  const double q = fma(r, 1.0 / 6.0, 0.5);
   const double p = fma(r * r, q, r);                       // exp(r) - 1
-  const int j = n & 255;
-  const int k = n >> 8;                                    // floor division
+  const int j = n & (SMC_EXP_TABLE - 1);
+  const int k = n >> 11;                                   // floor division
   const double tj = m.exp2tab[j];
   const double y = fma(tj, p, tj);
   return __hiloint2double(__double2hiint(y) + (k << 20), __double2loint(y));
@@ -53,10 +70,10 @@ __device__ __forceinline__ double sR(const Mech &m, int k, double T, double lnT)
   return c[0] * lnT + c[1] + T * (c[2] + T * (c[3] + T * (c[4] + T * c[5])));
 }
 
-// g/RT = h/RT - s/R of species k, folded into one polynomial in T plus the
-// 1/T and ln T terms (the same value as hR(T)/T - sR(T) in fewer operations).
-__device__ __forceinline__ double gRT(const Mech &m, int k, double T, double invT, double lnT) {
-  const double *c = m.gR[k];
+// g/RT - ln W_k of species k: h/RT - s/R folded into one polynomial in T
+// plus the 1/T and ln T terms, with -ln W_k in the constant term.
+__device__ __forceinline__ double gRT_W(const Mech &m, int k, double T, double invT, double lnT) {
+  const double *c = m.gW[k];
   const double poly = T * (c[3] + T * (c[4] + T * (c[5] + T * c[6])));
   return fma(c[0], invT, fma(c[2], lnT, c[1] + poly));
 }
@@ -109,16 +126,18 @@ __device__ __forceinline__ bool newton_T(const Mech &m, const double *Y, double 
 // rho*omega_k (g/(cm^3 s)) by mass action with reversible Arrhenius rates and
 // equilibrium constants from the Gibbs energies.  wdot[k] is overwritten.
 //
-// With g_k = g_k/(RT), a per-cell shift s (the species mean of g), z_k =
-// c_k exp(g_k - s) and P = (R_u T / p_atm) exp(s), the net rate
+// With G_k = g_k/(RT) - ln W_k, a per-cell shift s (the species mean of G),
+// z_k = rho Y_k exp(G_k - s) = c_k exp(g_k/RT - s) and P = (R_u T / p_atm) exp(s),
+// the net rate
 //   q = k_f prod c^nu' - (k_f / K_c) prod c^nu''
 // equals
-//   q = exp(ln k_f - sum_reac nu' (g - s)) (prod_reac z^nu' - P^dnu prod_prod z^nu'')
-// exactly (the exponential factors cancel), which needs one exponential per
-// reaction and one per species instead of two per reaction.  The shift keeps
-// z and the prefactor inside the FP64 range when the species' g spread over
-// less than 400 (checked by smc_create for 200..3500 K) with at most three
-// molecules per reaction side.
+//   q = exp(ln k_f - sum_reac nu' (ln W + G - s)) (prod_reac z^nu' - P^dnu prod_prod z^nu'')
+// exactly (the exponential factors cancel; the shift may be any number), which
+// needs one exponential per reaction and one per species instead of two per
+// reaction.  sum nu' ln W is folded into ln A when the mechanism is packed.
+// The shift keeps z and the prefactor inside the FP64 range when G spreads
+// over less than 400 (checked when the mechanism is packed, 200..3500 K) with
+// at most three molecules per reaction side.
 __device__ __forceinline__ void production_rates(const Mech &m, const Reaction *__restrict__ rx,
                                                  double rho, double T, const double *Y,
                                                  double *wdot, const double *rhoY = nullptr) {
@@ -128,35 +147,134 @@ __device__ __forceinline__ void production_rates(const Mech &m, const Reaction *
   const double invT = 1.0 / T;
   double gs = 0.0;
   for (int k = 0; k < ns; ++k) {
-    g[k] = gRT(m, k, T, invT, lnT);   // g_k / (R T)
+    g[k] = gRT_W(m, k, T, invT, lnT);
     gs += g[k];
   }
   gs *= m.inv_ns;
   for (int k = 0; k < ns; ++k) {
     g[k] -= gs;
-    const double c = (rhoY ? rhoY[k] : rho * Y[k]) * m.invW[k];
-    z[k] = c * fast_exp(m, g[k]);
+    z[k] = (rhoY ? rhoY[k] : rho * Y[k]) * fast_exp(m, g[k]);
     wdot[k] = 0.0;
   }
-  // P^j for j = -4..4
+  // P^j for j = -3..3
   const double P1 = T * (kRu / kPatm) * fast_exp(m, gs), Pm1 = 1.0 / P1;
   const double P2 = P1 * P1, Pm2 = Pm1 * Pm1;
-  const double Ppow[9] = {Pm2 * Pm2, Pm2 * Pm1, Pm2, Pm1, 1.0, P1, P2, P2 * P1, P2 * P2};
+  const double Ppow[7] = {Pm2 * Pm1, Pm2, Pm1, 1.0, P1, P2, P2 * P1};
   for (int r = 0; r < m.nr; ++r) {
     const Reaction &R = rx[r];
-    double ex = R.lnA + R.b * lnT - R.Ea_R * invT;
-    double fwd = 1.0, rev = 1.0;
-    for (int i = 0; i < R.nf; ++i) {
-      const int k = R.fk[i];
-      ex -= R.fcd[i] * g[k];
-      for (int j = 0; j < R.fc[i]; ++j) fwd *= z[k];
-    }
-    for (int i = 0; i < R.nr_; ++i)
-      for (int j = 0; j < R.rc[i]; ++j) rev *= z[R.rk[i]];
-    const double q = fast_exp(m, ex) * fma(-Ppow[R.dn + 4], rev, fwd);
+    double ex = fma(R.b, lnT, fma(-R.Ea_R, invT, R.lnA));
+    for (int i = 0; i < R.nf; ++i) ex = fma(-R.fcd[i], g[R.fk[i]], ex);
+    double fwd = z[R.fm[0]], rev = z[R.rm[0]];
+    for (int i = 1; i < R.nfm; ++i) fwd *= z[R.fm[i]];
+    for (int i = 1; i < R.nrm; ++i) rev *= z[R.rm[i]];
+    const double q = fast_exp(m, ex) * fma(-Ppow[R.dn + 3], rev, fwd);
     for (int i = 0; i < R.nf; ++i) wdot[R.fk[i]] = fma(-R.fcw[i], q, wdot[R.fk[i]]);
     for (int i = 0; i < R.nr_; ++i) wdot[R.rk[i]] = fma(R.rcw[i], q, wdot[R.rk[i]]);
   }
+}
+
+// ---------------------------------------------------------------- mixed
+// Production rates with FP32 mantissas (the mixed-precision path).  The
+// Gibbs energies, the reaction exponents and the argument reduction of every
+// exponential stay in FP64 (their absolute errors become relative errors of
+// the rates); what follows the reduction -- exp(r) on |r| <= ln2/4096, the
+// products of concentrations, the two terms of q and the accumulation of
+// rho omega_k -- runs in FP32.  Values outside the float range (z_k, the
+// rate prefactors) are carried as a float mantissa m and an integer
+// exponent e, m 2^e.
+
+struct xf {
+  float m;
+  int e;
+};
+
+__device__ __forceinline__ xf xf_mul(xf a, xf b) { return xf{a.m * b.m, a.e + b.e}; }
+
+// x (double) as m 2^e with |m| in [1, 2) (mantissa truncated to 24 bits);
+// zero and subnormal x give 0
+__device__ __forceinline__ xf xf_from_double(double x) {
+  const long long b = __double_as_longlong(x);
+  const int eb = (int)((b >> 52) & 0x7ff);
+  const unsigned sign = (unsigned)((unsigned long long)b >> 63) << 31;
+  if (eb == 0) return xf{0.0f, 0};
+  return xf{__uint_as_float(sign | 0x3f800000u | (unsigned)((b >> 29) & 0x7fffff)), eb - 1023};
+}
+
+// m 2^e as a float; below the float range it is negligible and flushes to 0
+__device__ __forceinline__ float xf_to_float(xf a) {
+  if (a.e < -126) return 0.0f;
+  const int e = a.e < 127 ? a.e : 127;
+  return a.m * __int_as_float((e + 127) << 23);
+}
+
+// float to double in integer arithmetic (subnormals flush to zero)
+__device__ __forceinline__ double float_to_double(float f) {
+  const unsigned b = __float_as_uint(f);
+  const unsigned ef = (b >> 23) & 0xff;
+  const unsigned sign = b & 0x80000000u;
+  if (ef == 0) return __hiloint2double((int)sign, 0);
+  const unsigned ed = ef == 0xff ? 0x7ffu : ef - 127 + 1023;
+  return __hiloint2double((int)(sign | (ed << 20) | ((b & 0x7fffff) >> 3)), (int)(b << 29));
+}
+
+// exp(x) as m 2^e: the reduction x = n ln2/2048 + r of fast_exp in FP64
+// (three operations), then 2^(j/2048) (1 + r + r^2/2) in FP32 (the next
+// term, r^3/6 < 1e-12, is far below FP32 rounding)
+__device__ __forceinline__ xf exp_xf(const Mech &m, double x) {
+  if ((__double2hiint(x) & 0x7ff00000) >= ((1023 + 9) << 20)) {
+    if (x != x) return xf{__int_as_float(0x7fffffff), 0};
+    if (x > 709.0) x = 709.0;
+    if (x < -708.0) x = -708.0;
+  }
+  const double shift = 6755399441055744.0;                 // 1.5 * 2^52
+  const double u = fma(x, 2954.639443740597, shift);       // 2048 / ln 2
+  const double nd = u - shift;
+  const int n = __double2loint(u);
+  const float r = trunc_float(fma(-nd, 3.384507717577858e-4, x));   // ln2 / 2048
+  const float p = fmaf(0.5f * r, r, r);
+  const float t = m.exp2tabf[n & (SMC_EXP_TABLE - 1)];
+  return xf{fmaf(t, p, t), n >> 11};
+}
+
+// rho*omega_k as production_rates (same shift and rewrite of q), FP32 after
+// the reductions; wdot[k] is overwritten with the FP64 value of the FP32 sum.
+__device__ __forceinline__ void production_rates_m(const Mech &m, const Reaction *__restrict__ rx,
+                                                   double T, const double *rhoY, double *wdot) {
+  const int ns = m.ns;
+  double g[SMC_MAX_NS];
+  xf z[SMC_MAX_NS];
+  float wf[SMC_MAX_NS];
+  const double lnT = log(T);
+  const double invT = 1.0 / T;
+  double gs = 0.0;
+  for (int k = 0; k < ns; ++k) {
+    g[k] = gRT_W(m, k, T, invT, lnT);
+    gs += g[k];
+  }
+  gs *= m.inv_ns;
+  for (int k = 0; k < ns; ++k) {
+    g[k] -= gs;
+    z[k] = xf_mul(xf_from_double(rhoY[k]), exp_xf(m, g[k]));
+    wf[k] = 0.0f;
+  }
+  // P^j, j = -3..3
+  const xf P1 = xf_mul(xf_from_double(T * (kRu / kPatm)), exp_xf(m, gs));
+  const xf Pm1 = xf{1.0f / P1.m, -P1.e};
+  const xf P2 = xf_mul(P1, P1), Pm2 = xf_mul(Pm1, Pm1);
+  const xf Ppow[7] = {xf_mul(Pm2, Pm1), Pm2, Pm1, xf{1.0f, 0}, P1, P2, xf_mul(P2, P1)};
+  for (int r = 0; r < m.nr; ++r) {
+    const Reaction &R = rx[r];
+    double ex = fma(R.b, lnT, fma(-R.Ea_R, invT, R.lnA));
+    for (int i = 0; i < R.nf; ++i) ex = fma(-R.fcd[i], g[R.fk[i]], ex);
+    const xf E = exp_xf(m, ex);
+    xf fwd = z[R.fm[0]], rev = z[R.rm[0]];
+    for (int i = 1; i < R.nfm; ++i) fwd = xf_mul(fwd, z[R.fm[i]]);
+    for (int i = 1; i < R.nrm; ++i) rev = xf_mul(rev, z[R.rm[i]]);
+    const float q = xf_to_float(xf_mul(E, fwd)) - xf_to_float(xf_mul(xf_mul(E, Ppow[R.dn + 3]), rev));
+    for (int i = 0; i < R.nf; ++i) wf[R.fk[i]] = fmaf(-R.fcwf[i], q, wf[R.fk[i]]);
+    for (int i = 0; i < R.nr_; ++i) wf[R.rk[i]] = fmaf(R.rcwf[i], q, wf[R.rk[i]]);
+  }
+  for (int k = 0; k < ns; ++k) wdot[k] = float_to_double(wf[k]);
 }
 
 }  // namespace smc

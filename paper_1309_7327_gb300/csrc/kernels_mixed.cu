@@ -33,19 +33,6 @@ struct f2 {
   float h, l;
 };
 
-// Truncating double -> float conversion in integer arithmetic (keeps the
-// FP64 pipe free): the top 23 stored mantissa bits are kept; magnitudes below
-// the float normal range flush to zero.  Exact when x has at most 24
-// significant bits.
-__device__ __forceinline__ float trunc_float(double x) {
-  const long long b = __double_as_longlong(x);
-  const int e = (int)((b >> 52) & 0x7ff) - 1023 + 127;
-  const unsigned sign = (unsigned)((unsigned long long)b >> 63) << 31;
-  if (e <= 0) return __uint_as_float(sign);
-  if (e >= 255) return __uint_as_float(sign | 0x7f800000u);
-  return __uint_as_float(sign | ((unsigned)e << 23) | (unsigned)((b >> 29) & 0x7fffff));
-}
-
 // x = hi + lo with hi the truncation of x to 24 bits (exactly representable)
 // and lo the remainder truncated to 24 bits: about 48 significant bits, one
 // FP64 operation.
@@ -432,7 +419,7 @@ __global__ void __launch_bounds__(128) k_final_m(const DevState s, const double 
                                                  double *__restrict__ dU, int transport,
                                                  int chemistry) {
   const Mech &m = *s.mech;
-  const int ns = s.ns, nv = s.nv;
+  const int ns = s.ns;
   const size_t NG = (size_t)s.nghost, NI = (size_t)s.ncells;
   const float *__restrict__ Qf = reinterpret_cast<const float *>(s.Q);
   const float *__restrict__ divf = reinterpret_cast<const float *>(s.divacc);
@@ -442,14 +429,14 @@ __global__ void __launch_bounds__(128) k_final_m(const DevState s, const double 
     double add[SMC_MAX_NS];
     for (int k = 0; k < ns; ++k) add[k] = 0.0;
     if (chemistry) {
-      // temperature from the conserved state, then the FP64 rates
-      double Uc[5 + SMC_MAX_NS], wd[SMC_MAX_NS], Y[SMC_MAX_NS];
-      for (int c = 0; c < nv; ++c) Uc[c] = U[(size_t)c * NI + i];
-      const double invrho = 1.0 / Uc[0];
-      for (int k = 0; k < ns; ++k) Y[k] = Uc[5 + k] * invrho;
+      // the temperature of the primitive pass, then the rates (FP64, or with
+      // FP32 mantissas when SMC_OPT_RATES is 1)
+      double rhoY[SMC_MAX_NS], wd[SMC_MAX_NS];
+      for (int k = 0; k < ns; ++k) rhoY[k] = U[(size_t)(5 + k) * NI + i];
       const f2 Tp = get_pair(Qf, NG, PM_T, g);
       const double T = (double)Tp.h + (double)Tp.l;
-      production_rates(m, s.rx, Uc[0], T, Y, wd);
+      if (s.opt.rates32) production_rates_m(m, s.rx, T, rhoY, wd);
+      else production_rates(m, s.rx, 0.0, T, nullptr, wd, rhoY);
       for (int k = 0; k < ns; ++k) add[k] = wd[k];
     }
     if (transport) {
@@ -512,6 +499,476 @@ void launch_march_m(const DevState &s, int dir, float *dUf, int first, cudaStrea
 void launch_final_m(const DevState &s, const double *U, const float *dUf, double *dU, int transport,
                     int chemistry, cudaStream_t st) {
   k_final_m<<<grid_for(s.ncells, 128), 128, 0, st>>>(s, U, dUf, dU, transport, chemistry);
+}
+
+
+
+// ------------------------------------------------------------ k_march_m2
+// The same terms as k_march_m, organised for data reuse.  Each thread walks
+// its line segment in chunks of up to M2_CH cells.  Every field is held in a
+// 9-cell register window (cells c-4 .. c+4 of the current cell c) that slides
+// by one cell per step, so a field value is loaded once per cell rather than
+// once per face or per stencil point.  The terms are taken in sub-passes over
+// small groups of fields (momentum, heat, convective fluxes, correction
+// velocity, then one species at a time) to bound the live registers; the
+// per-cell energy, correction velocity, species divergence sum and species
+// narrow term are carried between sub-passes in shared memory.
+constexpr int M2_CH = 16;
+constexpr int M2_NT = 128;
+
+namespace m2 {
+
+struct Win {
+  const float *__restrict__ Qf;
+  const float *__restrict__ Gf;
+  size_t NG;
+  long long gb;   // ghosted index of the chunk's first cell
+  int sg;
+  __device__ __forceinline__ float s(int plane, int r) const {
+    return __ldg(Qf + (size_t)plane * NG + gb + (long long)r * sg);
+  }
+  __device__ __forceinline__ float g(int plane, int r) const {
+    return __ldg(Gf + (size_t)plane * NG + gb + (long long)r * sg);
+  }
+  __device__ __forceinline__ f2 p(int plane, int r) const {
+    f2 v;
+    v.h = __ldg(Qf + (size_t)plane * NG + gb + (long long)r * sg);
+    v.l = __ldg(Qf + (size_t)(plane + 1) * NG + gb + (long long)r * sg);
+    return v;
+  }
+};
+
+// v[n] = sum_m a[o+m] M[m][n] for n != 3
+__device__ __forceinline__ void vm(const MarchParamsM &P, const float *a, int o, float *v) {
+#pragma unroll
+  for (int nn = 0; nn < 8; ++nn) {
+    float acc = 0.0f;
+#pragma unroll
+    for (int mm = 0; mm < 8; ++mm)
+      if (nn != 3 && mm - nn <= 4 && nn - mm <= 4) acc = fmaf(a[o + mm], P.M[mm][nn], acc);
+    v[nn] = acc;
+  }
+}
+// w[m] = sum_{n != 3} M[m][n] (x[o+n] - x[o+3])
+__device__ __forceinline__ void mv(const MarchParamsM &P, const f2 *x, int o, float *w) {
+  float d[8];
+#pragma unroll
+  for (int t = 0; t < 8; ++t) d[t] = (t == 3) ? 0.0f : diff(x[o + t], x[o + 3]);
+#pragma unroll
+  for (int mm = 0; mm < 8; ++mm) {
+    float acc = 0.0f;
+#pragma unroll
+    for (int t = 0; t < 8; ++t)
+      if (t != 3 && mm - t <= 4 && t - mm <= 4) acc = fmaf(P.M[mm][t], d[t], acc);
+    w[mm] = acc;
+  }
+}
+// sum_{n != 3} v[n] (x[o+n] - x[o+3])
+__device__ __forceinline__ float dp(const float *v, const f2 *x, int o) {
+  float acc = 0.0f;
+#pragma unroll
+  for (int t = 0; t < 8; ++t)
+    if (t != 3) acc = fmaf(v[t], diff(x[o + t], x[o + 3]), acc);
+  return acc;
+}
+// sum_t a[o+t] w[t]
+__device__ __forceinline__ float ds(const float *a, int o, const float *w) {
+  float acc = 0.0f;
+#pragma unroll
+  for (int t = 0; t < 8; ++t) acc = fmaf(a[o + t], w[t], acc);
+  return acc;
+}
+template <typename T>
+__device__ __forceinline__ void slide(T *w) {
+#pragma unroll
+  for (int i = 0; i < 8; ++i) w[i] = w[i + 1];
+}
+// centred D at the middle (index 4) of a 9-cell window
+__device__ __forceinline__ float Dp(const MarchParamsM &P, const f2 *w) {
+  float acc = 0.0f;
+#pragma unroll
+  for (int nn = 1; nn <= 4; ++nn) acc = fmaf(P.D[nn - 1], diff(w[4 + nn], w[4 - nn]), acc);
+  return acc;
+}
+__device__ __forceinline__ float Ds(const MarchParamsM &P, const float *w) {
+  float acc = 0.0f;
+#pragma unroll
+  for (int nn = 1; nn <= 4; ++nn) acc = fmaf(P.D[nn - 1], w[4 + nn] - w[4 - nn], acc);
+  return acc;
+}
+
+__device__ __forceinline__ void put(float *__restrict__ dUf, size_t NI, int comp, long long i, float v,
+                                    bool store) {
+  float *q = dUf + (size_t)comp * NI + i;
+  if (store) *q = v; else *q += v;
+}
+
+// transverse momentum fluxes rho u_d u_t - eta u_d,t (t = e, f) at window offset r
+template <int DIR>
+__device__ __forceinline__ void flux_ef(const Win &x, int r, f2 &fe, f2 &ff) {
+  constexpr int E_ = (DIR + 1) % 3, F_ = (DIR + 2) % 3;
+  const f2 m = mul(x.p(PM_RHO, r), x.p(PM_U + 2 * DIR, r));
+  fe = mul(m, x.p(PM_U + 2 * E_, r));
+  ff = mul(m, x.p(PM_U + 2 * F_, r));
+  const float eta = x.s(PM_ETA, r);
+  fe.l -= eta * x.g(3 * E_ + DIR, r);
+  ff.l -= eta * x.g(3 * F_ + DIR, r);
+}
+
+// energy flux rho H u_d - [c23 (u_e,e + u_f,f) u_d + eta (u_d,e u_e + u_d,f u_f)]
+template <int DIR>
+__device__ __forceinline__ f2 flux_E(const Win &x, int r) {
+  constexpr int E_ = (DIR + 1) % 3, F_ = (DIR + 2) % 3;
+  const f2 ud = x.p(PM_U + 2 * DIR, r), ue = x.p(PM_U + 2 * E_, r), uf = x.p(PM_U + 2 * F_, r);
+  const float eta = x.s(PM_ETA, r);
+  const float tdiv = x.s(PM_C23, r) * (x.g(3 * E_ + E_, r) + x.g(3 * F_ + F_, r));
+  f2 fE = mul(x.p(PM_RHOH, r), ud);
+  fE.l -= tdiv * (ud.h + ud.l) +
+          eta * (x.g(3 * E_ + DIR, r) * (ue.h + ue.l) + x.g(3 * F_ + DIR, r) * (uf.h + uf.l));
+  return fE;
+}
+
+}  // namespace m2
+
+template <int DIR>
+__global__ void __launch_bounds__(M2_NT, 3) k_march_m2(const DevState s, const MarchParamsM P,
+                                                       float *__restrict__ dUf, int first) {
+  using namespace m2;
+  __shared__ float sE[M2_CH][M2_NT], sV[M2_CH][M2_NT], sN[M2_CH][M2_NT], sO[M2_CH][M2_NT];
+  const int tid = threadIdx.x;
+  const long long item = blockIdx.x * (long long)blockDim.x + tid;
+  if (item >= s.nlines[DIR]) return;   // no block-wide barrier below
+  const LineItem L = s.lines[DIR][item];
+  constexpr int E_ = (DIR + 1) % 3, F_ = (DIR + 2) % 3;
+  const int ns = s.ns, mode = s.opt.mode, ref = s.opt.ref;
+  const size_t NI = (size_t)s.ncells;
+  float *__restrict__ divf = reinterpret_cast<float *>(s.divacc);
+  const bool st = first != 0;
+  Win x;
+  x.Qf = reinterpret_cast<const float *>(s.Q);
+  x.Gf = reinterpret_cast<const float *>(s.G);
+  x.NG = (size_t)s.nghost;
+  x.sg = L.sg;
+
+  for (int c0 = 0; c0 < L.len; c0 += M2_CH) {
+    const int n = min(M2_CH, L.len - c0);
+    x.gb = L.g0 + (long long)c0 * L.sg;
+    const long long ib = L.i0 + (long long)c0 * L.si;
+    for (int c = 0; c < n; ++c) {
+      sE[c][tid] = 0.0f;
+      sN[c][tid] = 0.0f;
+    }
+
+    // (c43 u_d,d)_d and (c43 (u_d^2/2)_d)_d
+    {
+      float a[9];
+      f2 u[9], k[9];
+#pragma unroll
+      for (int i = 0; i < 9; ++i) {
+        a[i] = x.s(PM_C43, i - 4);
+        u[i] = x.p(PM_U + 2 * DIR, i - 4);
+        k[i] = x.p(PM_KX + 2 * DIR, i - 4);
+      }
+      float v[8];
+      vm(P, a, 0, v);
+      float Hm = dp(v, u, 0), He = dp(v, k, 0);
+#pragma unroll 1
+      for (int c = 0; c < n; ++c) {
+        vm(P, a, 1, v);
+        const float Hm2 = dp(v, u, 1), He2 = dp(v, k, 1);
+        put(dUf, NI, 1 + DIR, ib + (long long)c * L.si, Hm2 - Hm, st);
+        sE[c][tid] += He2 - He;
+        Hm = Hm2;
+        He = He2;
+        if (c + 1 < n) {
+          slide(a); slide(u); slide(k);
+          a[8] = x.s(PM_C43, c + 5);
+          u[8] = x.p(PM_U + 2 * DIR, c + 5);
+          k[8] = x.p(PM_KX + 2 * DIR, c + 5);
+        }
+      }
+    }
+    // (eta u_t,d)_d and (eta (u_t^2/2)_d)_d for the two transverse components t
+#pragma unroll 1
+    for (int tt = 0; tt < 2; ++tt) {
+      const int t = tt == 0 ? E_ : F_;
+      float a[9];
+      f2 u[9], k[9];
+#pragma unroll
+      for (int i = 0; i < 9; ++i) {
+        a[i] = x.s(PM_ETA, i - 4);
+        u[i] = x.p(PM_U + 2 * t, i - 4);
+        k[i] = x.p(PM_KX + 2 * t, i - 4);
+      }
+      float v[8];
+      vm(P, a, 0, v);
+      float Hm = dp(v, u, 0), He = dp(v, k, 0);
+#pragma unroll 1
+      for (int c = 0; c < n; ++c) {
+        vm(P, a, 1, v);
+        const float Hm2 = dp(v, u, 1), He2 = dp(v, k, 1);
+        put(dUf, NI, 1 + t, ib + (long long)c * L.si, Hm2 - Hm, st);
+        sE[c][tid] += He2 - He;
+        Hm = Hm2;
+        He = He2;
+        if (c + 1 < n) {
+          slide(a); slide(u); slide(k);
+          a[8] = x.s(PM_ETA, c + 5);
+          u[8] = x.p(PM_U + 2 * t, c + 5);
+          k[8] = x.p(PM_KX + 2 * t, c + 5);
+        }
+      }
+    }
+    // (lambda T_d)_d, then (A_p p_d)_d
+#pragma unroll 1
+    for (int pass = 0; pass < 2; ++pass) {
+      const int pc = pass == 0 ? PM_LAM : PM_AP, pf = pass == 0 ? PM_T : PM_P;
+      float a[9];
+      f2 f[9];
+#pragma unroll
+      for (int i = 0; i < 9; ++i) {
+        a[i] = x.s(pc, i - 4);
+        f[i] = x.p(pf, i - 4);
+      }
+      float w[8];
+      mv(P, f, 0, w);
+      float H = ds(a, 0, w);
+#pragma unroll 1
+      for (int c = 0; c < n; ++c) {
+        mv(P, f, 1, w);
+        const float H2 = ds(a, 1, w);
+        sE[c][tid] += H2 - H;
+        H = H2;
+        if (c + 1 < n) {
+          slide(a); slide(f);
+          a[8] = x.s(pc, c + 5);
+          f[8] = x.p(pf, c + 5);
+        }
+      }
+    }
+    // -D_d(rho u_d) and -D_d(rho u_d u_d)
+    {
+      f2 ms[9], fd[9];
+#pragma unroll
+      for (int i = 0; i < 9; ++i) {
+        const f2 ud = x.p(PM_U + 2 * DIR, i - 4);
+        ms[i] = mul(x.p(PM_RHO, i - 4), ud);
+        fd[i] = mul(ms[i], ud);
+      }
+#pragma unroll 1
+      for (int c = 0; c < n; ++c) {
+        const long long i = ib + (long long)c * L.si;
+        put(dUf, NI, 0, i, -Dp(P, ms), st);
+        sO[c][tid] = Dp(P, fd);
+        if (c + 1 < n) {
+          slide(ms); slide(fd);
+          const f2 ud = x.p(PM_U + 2 * DIR, c + 5);
+          ms[8] = mul(x.p(PM_RHO, c + 5), ud);
+          fd[8] = mul(ms[8], ud);
+        }
+      }
+    }
+    // -D_d(p - c23 (u_e,e + u_f,f)) and the convective part above
+    {
+      f2 p[9];
+      float td[9];
+#pragma unroll
+      for (int i = 0; i < 9; ++i) {
+        p[i] = x.p(PM_P, i - 4);
+        td[i] = x.s(PM_C23, i - 4) * (x.g(3 * E_ + E_, i - 4) + x.g(3 * F_ + F_, i - 4));
+      }
+#pragma unroll 1
+      for (int c = 0; c < n; ++c) {
+        put(dUf, NI, 1 + DIR, ib + (long long)c * L.si, Ds(P, td) - sO[c][tid] - Dp(P, p), false);
+        if (c + 1 < n) {
+          slide(p); slide(td);
+          p[8] = x.p(PM_P, c + 5);
+          td[8] = x.s(PM_C23, c + 5) * (x.g(3 * E_ + E_, c + 5) + x.g(3 * F_ + F_, c + 5));
+        }
+      }
+    }
+    // -D_d of the transverse momentum fluxes
+    {
+      f2 fe[9], ff[9];
+#pragma unroll
+      for (int i = 0; i < 9; ++i) flux_ef<DIR>(x, i - 4, fe[i], ff[i]);
+#pragma unroll 1
+      for (int c = 0; c < n; ++c) {
+        const long long i = ib + (long long)c * L.si;
+        put(dUf, NI, 1 + E_, i, -Dp(P, fe), false);
+        put(dUf, NI, 1 + F_, i, -Dp(P, ff), false);
+        if (c + 1 < n) {
+          slide(fe); slide(ff);
+          flux_ef<DIR>(x, c + 5, fe[8], ff[8]);
+        }
+      }
+    }
+    // -D_d of the energy flux
+    {
+      f2 fE[9];
+#pragma unroll
+      for (int i = 0; i < 9; ++i) fE[i] = flux_E<DIR>(x, i - 4);
+#pragma unroll 1
+      for (int c = 0; c < n; ++c) {
+        sE[c][tid] -= Dp(P, fE);
+        if (c + 1 < n) {
+          slide(fE);
+          fE[8] = flux_E<DIR>(x, c + 5);
+        }
+      }
+    }
+    // correction velocity V_c,d = -(sum_l rhoD_l X_l,d + (sum_l B_l) p_d)
+    if (mode == 0) {
+      {
+        f2 p[9];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) p[i] = x.p(PM_P, i - 4);
+#pragma unroll 1
+        for (int c = 0; c < n; ++c) {
+          sV[c][tid] = -x.s(PM_SB, c) * Dp(P, p);
+          if (c + 1 < n) {
+            slide(p);
+            p[8] = x.p(PM_P, c + 5);
+          }
+        }
+      }
+#pragma unroll 1
+      for (int l = 0; l < ns; ++l) {
+        f2 X[9];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) X[i] = x.p(pmX(ns, l), i - 4);
+#pragma unroll 1
+        for (int c = 0; c < n; ++c) {
+          sV[c][tid] -= x.s(pmRD(ns, l), c) * Dp(P, X);
+          if (c + 1 < n) {
+            slide(X);
+            X[8] = x.p(pmX(ns, l), c + 5);
+          }
+        }
+      }
+    }
+    // species, one at a time
+#pragma unroll 1
+    for (int k = 0; k < ns; ++k) {
+      const bool narrow = !(mode == 1 && k == ref);
+      if (narrow) {
+        // (rhoD_k X_k,d)_d and its energy part (rhoD_k h'_k X_k,d)_d
+        {
+          f2 X[9];
+          float rd[9], rdh[9];
+#pragma unroll
+          for (int i = 0; i < 9; ++i) {
+            X[i] = x.p(pmX(ns, k), i - 4);
+            rd[i] = x.s(pmRD(ns, k), i - 4);
+            rdh[i] = x.s(pmRDH(ns, k), i - 4);
+          }
+          float w[8];
+          mv(P, X, 0, w);
+          float H = ds(rd, 0, w), He = ds(rdh, 0, w);
+#pragma unroll 1
+          for (int c = 0; c < n; ++c) {
+            mv(P, X, 1, w);
+            const float H2 = ds(rd, 1, w), He2 = ds(rdh, 1, w);
+            sO[c][tid] = H2 - H;
+            sE[c][tid] += He2 - He;
+            H = H2;
+            He = He2;
+            if (c + 1 < n) {
+              slide(X); slide(rd); slide(rdh);
+              X[8] = x.p(pmX(ns, k), c + 5);
+              rd[8] = x.s(pmRD(ns, k), c + 5);
+              rdh[8] = x.s(pmRDH(ns, k), c + 5);
+            }
+          }
+        }
+        // (B_k p_d)_d
+        {
+          f2 p[9];
+          float B[9];
+#pragma unroll
+          for (int i = 0; i < 9; ++i) {
+            p[i] = x.p(PM_P, i - 4);
+            B[i] = x.s(pmB(ns, k), i - 4);
+          }
+          float w[8];
+          mv(P, p, 0, w);
+          float H = ds(B, 0, w);
+#pragma unroll 1
+          for (int c = 0; c < n; ++c) {
+            mv(P, p, 1, w);
+            const float H2 = ds(B, 1, w);
+            const float o = sO[c][tid] + (H2 - H);
+            sO[c][tid] = o;
+            sN[c][tid] += o;
+            H = H2;
+            if (c + 1 < n) {
+              slide(p); slide(B);
+              p[8] = x.p(PM_P, c + 5);
+              B[8] = x.s(pmB(ns, k), c + 5);
+            }
+          }
+        }
+      }
+      // -D_d(rho Y_k u_d) and Y_k,d V_c,d
+      {
+        f2 Fk[9], Yk[9];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+          Fk[i] = mul(x.p(pmRY(ns, k), i - 4), x.p(PM_U + 2 * DIR, i - 4));
+          if (mode == 0) Yk[i] = x.p(pmY(ns, k), i - 4);
+        }
+#pragma unroll 1
+        for (int c = 0; c < n; ++c) {
+          float o = (narrow ? sO[c][tid] : 0.0f) - Dp(P, Fk);
+          if (mode == 0) o = fmaf(Dp(P, Yk), sV[c][tid], o);
+          put(dUf, NI, 5 + k, ib + (long long)c * L.si, o, st);
+          if (c + 1 < n) {
+            slide(Fk);
+            Fk[8] = mul(x.p(pmRY(ns, k), c + 5), x.p(PM_U + 2 * DIR, c + 5));
+            if (mode == 0) {
+              slide(Yk);
+              Yk[8] = x.p(pmY(ns, k), c + 5);
+            }
+          }
+        }
+      }
+    }
+    if (mode == 1) {
+      for (int c = 0; c < n; ++c)
+        put(dUf, NI, 5 + ref, ib + (long long)c * L.si, -sN[c][tid], false);
+    } else {
+      // h,d V_c,d
+      f2 hm[9];
+#pragma unroll
+      for (int i = 0; i < 9; ++i) hm[i] = x.p(PM_HMIX, i - 4);
+#pragma unroll 1
+      for (int c = 0; c < n; ++c) {
+        sE[c][tid] = fmaf(Dp(P, hm), sV[c][tid], sE[c][tid]);
+        if (c + 1 < n) {
+          slide(hm);
+          hm[8] = x.p(PM_HMIX, c + 5);
+        }
+      }
+      for (int c = 0; c < n; ++c) {
+        const long long i = ib + (long long)c * L.si;
+        if (st) divf[i] = sN[c][tid]; else divf[i] += sN[c][tid];
+      }
+    }
+    for (int c = 0; c < n; ++c) put(dUf, NI, 4, ib + (long long)c * L.si, sE[c][tid], st);
+  }
+}
+
+void launch_march_m2(const DevState &s, int dir, float *dUf, int first, cudaStream_t st) {
+  MarchParamsM P;
+  for (int a = 0; a < 8; ++a)
+    for (int b = 0; b < 8; ++b) P.M[a][b] = (float)s.hcoef->M[dir][a][b];
+  for (int k = 0; k < 4; ++k) P.D[k] = (float)s.hcoef->D[dir][k];
+  const long long n = s.nlines[dir];
+  if (n == 0) return;
+  const int blocks = (int)((n + M2_NT - 1) / M2_NT);
+  if (dir == 0) k_march_m2<0><<<blocks, M2_NT, 0, st>>>(s, P, dUf, first);
+  else if (dir == 1) k_march_m2<1><<<blocks, M2_NT, 0, st>>>(s, P, dUf, first);
+  else k_march_m2<2><<<blocks, M2_NT, 0, st>>>(s, P, dUf, first);
 }
 
 }  // namespace smc

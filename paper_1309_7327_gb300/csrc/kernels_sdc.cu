@@ -33,7 +33,9 @@ void launch_combo(const double *in, double *out, const Combo &cb, long long n, c
 }
 
 // Reaction right-hand side f2 at one cell from its conserved state.  Tg is
-// the Newton first guess on entry and the temperature on return.
+// the Newton first guess on entry and the temperature on return.  MIX: the
+// mixed-precision rates (FP32 after the FP64 reductions).
+template <bool MIX>
 __device__ __forceinline__ bool cell_reactions(const DevState &s, const double *Uc, double *f2,
                                                unsigned &flag, double &Tg) {
   const Mech &m = *s.mech;
@@ -51,13 +53,15 @@ __device__ __forceinline__ bool cell_reactions(const DevState &s, const double *
   if (!(rho > 0.0) || !(T > 0.0)) flag |= ST_NONPHYS;
   if (!isfinite(rho) || !isfinite(T)) flag |= ST_NONFINITE;
   if (s.opt.reactions && m.nr > 0) {
-    production_rates(m, s.rx, rho, T, Y, f2, Uc + 5);
+    if (MIX) production_rates_m(m, s.rx, T, Uc + 5, f2);
+    else production_rates(m, s.rx, rho, T, Y, f2, Uc + 5);
   } else {
     for (int k = 0; k < ns; ++k) f2[k] = 0.0;
   }
   return ok;
 }
 
+template <bool MIX>
 __global__ void __launch_bounds__(128) k_chem_only(const DevState s, const double *__restrict__ U,
                                                    double *__restrict__ F2) {
   const int ns = s.ns, nv = s.nv;
@@ -68,21 +72,25 @@ __global__ void __launch_bounds__(128) k_chem_only(const DevState s, const doubl
     for (int c = 0; c < nv; ++c) Uc[c] = U[(size_t)c * NI + i];
     unsigned flag = 0;
     double Tg = s.opt.T0;
-    cell_reactions(s, Uc, f2, flag, Tg);
+    cell_reactions<MIX>(s, Uc, f2, flag, Tg);
     if (flag) atomicOr(s.status, flag);
     for (int k = 0; k < ns; ++k) F2[(size_t)k * NI + i] = f2[k];
   }
 }
 
 void launch_chem_only(const DevState &s, const double *U, double *F2, cudaStream_t st) {
-  k_chem_only<<<grid_for(s.ncells, 128), 128, 0, st>>>(s, U, F2);
+  if (s.opt.rates32) k_chem_only<true><<<grid_for(s.ncells, 128), 128, 0, st>>>(s, U, F2);
+  else k_chem_only<false><<<grid_for(s.ncells, 128), 128, 0, st>>>(s, U, F2);
 }
 
 // Fine substeps q = q0 .. q0+nsub-1 of eq. mrupdate for every cell:
 //   U_{q+1} = U_q + dt_q [f1(U^{k+1}_p) - f1(U^k_p)] + dt_q [f2(U^{k+1}_q) - f2(U^k_q)]
 //             + dt (S22 F2^k)_q + dt (S21 F1^k)_q
 // f1 is frozen at the coarse node p on the left; f2 (reactions, species
-// components only) is evaluated at every fine node.
+// components only) is evaluated at every fine node.  f1(U^k_p) and f2(U^k_q)
+// are nodes of the two quadratures, so their -dt_q terms are folded into the
+// weights s21[.][p] and s22[.][q - q0] on the host.
+template <bool MIX>
 __global__ void __launch_bounds__(128) k_fine_chain(const DevState s, const double *__restrict__ Uin,
                                                     double *__restrict__ Uout, const FineChain fc) {
   const int ns = s.ns, nv = s.nv, M1 = fc.M1;
@@ -97,7 +105,7 @@ __global__ void __launch_bounds__(128) k_fine_chain(const DevState s, const doub
     double Tg = s.opt.T0;
     for (int sidx = 0; sidx < fc.nsub; ++sidx) {
       if (sidx > 0 || fc.eval_first) {
-        cell_reactions(s, Uc, f2, flag, Tg);
+        cell_reactions<MIX>(s, Uc, f2, flag, Tg);
         for (int k = 0; k < ns; ++k) fc.F2new[sidx][(size_t)k * NI + i] = f2[k];
       } else {
         for (int k = 0; k < ns; ++k) f2[k] = fc.F2old[0][(size_t)k * NI + i];
@@ -105,19 +113,19 @@ __global__ void __launch_bounds__(128) k_fine_chain(const DevState s, const doub
       const double dq = fc.dtq[sidx];
       for (int c = 0; c < nv; ++c) {
         const size_t o = (size_t)c * NI + i;
-        double acc = dq * (fc.F1new_p[o] - fc.F1old_p[o]);
-        for (int j = 0; j <= M1; ++j) acc += fc.s21[sidx][j] * fc.F1old[j][o];
+        double acc = dq * fc.F1new_p[o];
+        for (int j = 0; j <= M1; ++j) acc = fma(fc.s21[sidx][j], fc.F1old[j][o], acc);
         if (c >= 5) {
           const int k = c - 5;
           const size_t ok = (size_t)k * NI + i;
-          acc += dq * (f2[k] - fc.F2old[sidx][ok]);
-          for (int t = 0; t <= fc.nsub; ++t) acc += fc.s22[sidx][t] * fc.F2old[t][ok];
+          acc = fma(dq, f2[k], acc);
+          for (int t = 0; t <= fc.nsub; ++t) acc = fma(fc.s22[sidx][t], fc.F2old[t][ok], acc);
         }
         Uc[c] += acc;
       }
     }
     if (fc.eval_last) {
-      cell_reactions(s, Uc, f2, flag, Tg);
+      cell_reactions<MIX>(s, Uc, f2, flag, Tg);
       for (int k = 0; k < ns; ++k) fc.F2new[fc.nsub][(size_t)k * NI + i] = f2[k];
     }
     if (flag) atomicOr(s.status, flag);
@@ -178,9 +186,21 @@ void launch_transpose_x(const DevState &s, const void *src, void *dst, int plane
                                                  (const float *)src, (float *)dst, planes);
 }
 
+__global__ void __launch_bounds__(256) k_exp(const Mech *__restrict__ m, const double *__restrict__ x,
+                                             double *__restrict__ y, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    y[i] = fast_exp(*m, x[i]);
+}
+
+void launch_exp(const Mech *m, const double *x, double *y, long long n, cudaStream_t st) {
+  k_exp<<<grid_for(n, 256), 256, 0, st>>>(m, x, y, n);
+}
+
 void launch_fine_chain(const DevState &s, const double *Uin, double *Uout, const FineChain &fc,
                        cudaStream_t st) {
-  k_fine_chain<<<grid_for(s.ncells, 128), 128, 0, st>>>(s, Uin, Uout, fc);
+  if (s.opt.rates32) k_fine_chain<true><<<grid_for(s.ncells, 128), 128, 0, st>>>(s, Uin, Uout, fc);
+  else k_fine_chain<false><<<grid_for(s.ncells, 128), 128, 0, st>>>(s, Uin, Uout, fc);
 }
 
 }  // namespace smc

@@ -53,87 +53,6 @@ smc_status scratch_ptr(unsigned char **out) {
   return SMC_OK;
 }
 
-smc_status fill_mechanism(const smc_mechanism *mech, Mech &M, Reaction *rx) {
-  const int ns = mech->nspecies, nr = mech->nreactions;
-  if (ns < 1 || ns > SMC_MAX_NS || nr < 0 || nr > kMaxReactions) return SMC_ERR_ARG;
-  if (!mech->W || !mech->nasa7 || !mech->Le ||
-      (nr > 0 && (!mech->nu_f || !mech->nu_r || !mech->A || !mech->b || !mech->Ea)))
-    return SMC_ERR_ARG;
-  memset(&M, 0, sizeof(M));
-  M.ns = ns;
-  M.nr = nr;
-  for (int k = 0; k < ns; ++k) {
-    if (!(mech->W[k] > 0) || !(mech->Le[k] > 0)) return SMC_ERR_ARG;
-    const double *a = mech->nasa7 + 7 * k;
-    M.W[k] = mech->W[k];
-    M.invW[k] = 1.0 / mech->W[k];
-    M.Ru_W[k] = kRu / mech->W[k];
-    M.invLe[k] = 1.0 / mech->Le[k];
-    for (int i = 0; i < 5; ++i) M.cp[k][i] = a[i];
-    const double hT[6] = {a[5], a[0], a[1] / 2, a[2] / 3, a[3] / 4, a[4] / 5};
-    const double sR[6] = {a[0], a[6], a[1], a[2] / 2, a[3] / 3, a[4] / 4};
-    for (int i = 0; i < 6; ++i) {
-      M.hT[k][i] = hT[i];
-      M.sR[k][i] = sR[i];
-    }
-    const double gR[7] = {a[5], a[0] - a[6], -a[0], -a[1] / 2, -a[2] / 6, -a[3] / 12, -a[4] / 20};
-    for (int i = 0; i < 7; ++i) M.gR[k][i] = gR[i];
-  }
-  M.eta_ref = mech->eta_ref;
-  M.inv_T_ref = 1.0 / mech->T_ref;
-  M.eta_exp = mech->eta_exp;
-  M.inv_Pr = 1.0 / mech->Pr;
-  M.inv_ns = 1.0 / ns;
-  for (int k = 0; k < ns; ++k) {
-    for (int i = 0; i < 6; ++i) M.hTf[k][i] = (float)M.hT[k][i];
-    M.Ru_Wf[k] = (float)M.Ru_W[k];
-    M.invLef[k] = (float)M.invLe[k];
-  }
-  M.eta_ref_f = (float)M.eta_ref;
-  M.inv_T_ref_f = (float)M.inv_T_ref;
-  M.eta_exp_f = (float)M.eta_exp;
-  M.inv_Pr_f = (float)M.inv_Pr;
-  for (int j = 0; j < 256; ++j) M.exp2tab[j] = (double)exp2l((long double)j / 256.0L);
-  for (int r = 0; r < nr; ++r) {
-    Reaction &R = rx[r];
-    memset(&R, 0, sizeof(R));
-    if (!(mech->A[r] > 0)) return SMC_ERR_ARG;
-    R.lnA = log(mech->A[r]);
-    R.b = mech->b[r];
-    R.Ea_R = mech->Ea[r] / kRc;
-    double dnu = 0, mass = 0, scale = 0;
-    int mf = 0, mr = 0;
-    for (int k = 0; k < ns; ++k) {
-      const int f = mech->nu_f[r * ns + k], p = mech->nu_r[r * ns + k];
-      if (f < 0 || p < 0) return SMC_ERR_ARG;
-      if (f > 0) {
-        if (R.nf == SMC_MAX_SIDE) return SMC_ERR_ARG;
-        R.fk[R.nf] = k;
-        R.fcd[R.nf] = f;
-        R.fcw[R.nf] = f * mech->W[k];
-        R.fc[R.nf++] = f;
-        mf += f;
-      }
-      if (p > 0) {
-        if (R.nr_ == SMC_MAX_SIDE) return SMC_ERR_ARG;
-        R.rk[R.nr_] = k;
-        R.rcd[R.nr_] = p;
-        R.rcw[R.nr_] = p * mech->W[k];
-        R.rc[R.nr_++] = p;
-        mr += p;
-      }
-      dnu += p - f;
-      mass += (p - f) * mech->W[k];
-      scale += (p + f) * mech->W[k];
-    }
-    if (R.nf == 0 || R.nr_ == 0 || mf > 3 || mr > 3 || fabs(mass) > 1e-9 * scale)
-      return SMC_ERR_ARG;
-    R.dnu = dnu;
-    R.dn = (int)dnu;
-  }
-  return SMC_OK;
-}
-
 }  // namespace
 
 extern "C" smc_status smc_rhs_noalloc(const int n[3], const double dx[3],
@@ -174,8 +93,11 @@ extern "C" smc_status smc_rhs_noalloc(const int n[3], const double dx[3],
   unsigned char *hs = g_host_stage;
   Mech &M = *reinterpret_cast<Mech *>(hs + o_mech);
   Reaction *rx = reinterpret_cast<Reaction *>(hs + o_rx);
-  smc_status sm = fill_mechanism(mech, M, rx);
-  if (sm != SMC_OK) return sm;
+  {
+    std::vector<Reaction> hrx;   // host memory only
+    if (pack_mechanism(mech, kMaxReactions, M, hrx)) return SMC_ERR_ARG;
+    if (!hrx.empty()) memcpy(rx, hrx.data(), hrx.size() * sizeof(Reaction));
+  }
   Box &B = *reinterpret_cast<Box *>(hs + o_box);
   B.nx = n[0]; B.ny = n[1]; B.nz = n[2];
   B.gx = gx; B.gy = gy; B.gz = gz;

@@ -106,16 +106,22 @@ void node_to_node_matrix(const std::vector<double> &nodes, std::vector<double> &
 // `coarse` Gauss-Lobatto nodes.  S21 integrates the coarse interpolant between
 // fine nodes; S22 integrates the piecewise (per coarse interval) interpolant
 // of the fine values.
-void multirate_matrices(int coarse, int fine, std::vector<double> &t1, std::vector<double> &t2,
-                        std::vector<double> &S21, std::vector<double> &S22) {
+void multirate_matrices(int coarse, int fine, int repeat, std::vector<double> &t1,
+                        std::vector<double> &t2, std::vector<double> &S21,
+                        std::vector<double> &S22) {
   std::vector<double> g;
   lobatto_nodes(coarse, t1);
   lobatto_nodes(fine, g);
-  const int M1 = coarse - 1, per = fine - 1, M2 = M1 * per;
+  // every coarse interval holds `repeat` consecutive groups of `fine`
+  // Gauss-Lobatto nodes (type (b) for repeat = 1, type (c) otherwise);
+  // neighbouring groups share their end nodes
+  const int M1 = coarse - 1, sub = fine - 1, per = sub * repeat, M2 = M1 * per;
   std::vector<ld> T2(M2 + 1);
   for (int p = 0; p < M1; ++p)
-    for (int s = 0; s <= per; ++s)
-      T2[p * per + s] = (ld)t1[p] + ((ld)t1[p + 1] - (ld)t1[p]) * (ld)g[s];
+    for (int r = 0; r < repeat; ++r)
+      for (int s = 0; s <= sub; ++s)
+        T2[p * per + r * sub + s] =
+            (ld)t1[p] + ((ld)t1[p + 1] - (ld)t1[p]) * ((ld)r + (ld)g[s]) / (ld)repeat;
   t2.resize(M2 + 1);
   for (int q = 0; q <= M2; ++q) t2[q] = (double)T2[q];
   std::vector<ld> T1(t1.begin(), t1.end()), C1;
@@ -125,17 +131,19 @@ void multirate_matrices(int coarse, int fine, std::vector<double> &t1, std::vect
   for (int q = 0; q < M2; ++q)
     for (int j = 0; j <= M1; ++j)
       S21[q * (M1 + 1) + j] = (double)integral(C1, M1 + 1, j, T2[q], T2[q + 1]);
-  // the fine basis of one coarse interval, in the interval's own coordinate
-  // sigma = (t - t1_p) / (t1_{p+1} - t1_p) (the Lagrange basis is invariant
-  // under this affine map; it keeps the Vandermonde system well conditioned)
+  // the fine basis of one group, in the group's own coordinate
+  // sigma = (t - start) / width (the Lagrange basis is invariant under this
+  // affine map; it keeps the Vandermonde system well conditioned)
   std::vector<ld> G(g.begin(), g.end()), Cg;
   lagrange_coeffs(G, Cg);
   for (int p = 0; p < M1; ++p) {
-    const ld width = (ld)t1[p + 1] - (ld)t1[p];
-    for (int s = 0; s < per; ++s)
-      for (int t = 0; t <= per; ++t)
-        S22[(p * per + s) * (M2 + 1) + p * per + t] =
-            (double)(width * integral(Cg, per + 1, t, G[s], G[s + 1]));
+    const ld width = ((ld)t1[p + 1] - (ld)t1[p]) / (ld)repeat;
+    for (int r = 0; r < repeat; ++r) {
+      const int q0 = p * per + r * sub;
+      for (int s = 0; s < sub; ++s)
+        for (int t = 0; t <= sub; ++t)
+          S22[(q0 + s) * (M2 + 1) + q0 + t] = (double)(width * integral(Cg, sub + 1, t, G[s], G[s + 1]));
+    }
   }
 }
 

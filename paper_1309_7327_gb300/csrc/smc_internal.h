@@ -12,6 +12,7 @@
 #define SMC_MAX_NS 64
 #define SMC_MAX_SIDE 4        // species per reaction side
 #define SMC_GHOST 4           // ghost cells per side (8th-order stencils)
+#define SMC_EXP_TABLE 2048    // entries of the exponential's 2^(j/N) table
 
 namespace smc {
 
@@ -29,11 +30,13 @@ struct Mech {
   double cp[SMC_MAX_NS][5];       // cp/R = c0 + c1 T + ... + c4 T^4
   double hT[SMC_MAX_NS][6];       // h/R  = a6 + T (a1 + T (a2/2 + ...))
   double sR[SMC_MAX_NS][6];       // s/R  = a1 ln T + a7 + T (a2 + T (a3/2 + ...)) : {a1, a7, a2, a3/2, a4/3, a5/4}
-  double gR[SMC_MAX_NS][7];       // g/RT = a6/T + (a1 - a7) - a1 ln T + T (-a2/2 + T (-a3/6 + T (-a4/12 + T (-a5/20))))
-                                  //   : {a6, a1 - a7, -a1, -a2/2, -a3/6, -a4/12, -a5/20}
+  double gW[SMC_MAX_NS][7];       // g/RT - ln W_k = a6/T + (a1 - a7 - ln W_k) - a1 ln T
+                                  //   + T (-a2/2 + T (-a3/6 + T (-a4/12 + T (-a5/20))))
+                                  //   : {a6, a1 - a7 - ln W_k, -a1, -a2/2, -a3/6, -a4/12, -a5/20}
   double eta_ref, inv_T_ref, eta_exp, inv_Pr;
   double inv_ns;
-  double exp2tab[256];            // 2^(j/256), j = 0..255 (table of fast_exp)
+  double exp2tab[SMC_EXP_TABLE];  // 2^(j/2048) (table of fast_exp)
+  float exp2tabf[SMC_EXP_TABLE];  // the same rounded to float (mixed-precision rates)
   // float copies for the mixed-precision transport (no conversions in kernels)
   float hTf[SMC_MAX_NS][6];
   float Ru_Wf[SMC_MAX_NS];
@@ -42,18 +45,25 @@ struct Mech {
 };
 
 struct Reaction {
-  double lnA, b, Ea_R;            // Ea / R_c (K)
-  double dnu;                     // sum_k nu''_k - nu'_k
-  double fcd[SMC_MAX_SIDE];       // coefficients as doubles (no int->double
-  double rcd[SMC_MAX_SIDE];       //   conversions on the FP64 pipe)
+  double lnA;                     // ln A - sum_k nu'_k ln W_k
+  double b, Ea_R;                 // temperature exponent; Ea / R_c (K)
+  double fcd[SMC_MAX_SIDE];       // nu'_k as doubles (no int->double conversions)
   double fcw[SMC_MAX_SIDE];       // nu' W_k and nu'' W_k: production rates in g/(cm^3 s)
   double rcw[SMC_MAX_SIDE];       //   accumulate without a final multiply
+  float fcwf[SMC_MAX_SIDE];       // the same as floats (mixed-precision rates)
+  float rcwf[SMC_MAX_SIDE];
   int nf, nr_;                    // species on each side
-  int fk[SMC_MAX_SIDE], fc[SMC_MAX_SIDE];
-  int rk[SMC_MAX_SIDE], rc[SMC_MAX_SIDE];
-  int dn;                         // dnu as an integer, -4..4
+  int fk[SMC_MAX_SIDE];
+  int rk[SMC_MAX_SIDE];
+  int fm[3], rm[3];               // the molecules of each side (species repeated nu times)
+  int nfm, nrm;
+  int dn;                         // sum_k nu''_k - nu'_k, -3..3
   int pad;
 };
+
+// Pack and check a mechanism; nullptr on success, else the reason.
+const char *pack_mechanism(const smc_mechanism *mech, int max_reactions, Mech &M,
+                           std::vector<Reaction> &rx);
 
 // Geometry of one box in the ghosted (Q) and interior (U) layouts.
 struct Box {
@@ -77,6 +87,7 @@ struct Opts {
   int ref;
   int reactions;
   int maxit;
+  int rates32;                    // 1: production rates with FP32 mantissas (mixed precision only)
   double tol, T0, xi_ratio;
 };
 
@@ -107,8 +118,9 @@ enum : unsigned { ST_NONCONV = 1u, ST_NONPHYS = 2u, ST_NONFINITE = 4u };
 // Host-side quadrature (Gauss-Lobatto nodes, Lagrange integration matrices).
 void lobatto_nodes(int n, std::vector<double> &x);
 void node_to_node_matrix(const std::vector<double> &nodes, std::vector<double> &S);
-void multirate_matrices(int coarse, int fine, std::vector<double> &t1, std::vector<double> &t2,
-                        std::vector<double> &S21, std::vector<double> &S22);
+void multirate_matrices(int coarse, int fine, int repeat, std::vector<double> &t1,
+                        std::vector<double> &t2, std::vector<double> &S21,
+                        std::vector<double> &S22);
 
 // Kernel launchers (kernels_*.cu).
 struct DevState {
@@ -148,6 +160,7 @@ int nQm(int ns);
 void launch_prim_m(const DevState &s, const double *U, cudaStream_t st);
 void launch_grad_m(const DevState &s, cudaStream_t st);
 void launch_march_m(const DevState &s, int dir, float *dUf, int first, cudaStream_t st);
+void launch_march_m2(const DevState &s, int dir, float *dUf, int first, cudaStream_t st);
 void launch_final_m(const DevState &s, const double *U, const float *dUf, double *dU, int transport,
                     int chemistry, cudaStream_t st);
 
@@ -165,9 +178,10 @@ void launch_combo(const double *in, double *out, const Combo &cb, long long n, c
 struct FineChain {
   int q0, nsub, p, M1;
   double dtq[8];                  // dt * (t2[q+1] - t2[q])
-  double s21[8][5];               // dt * S21[q][j], j over coarse nodes
-  double s22[8][9];               // dt * S22[q][q0 + t], t over the group's nodes
-  const double *F1new_p, *F1old_p;   // coarse F at node p (new / old sweep), NV comps
+  double s21[8][5];               // dt * S21[q][j] - [j == p] dtq: coarse-node weights with the
+                                  //   -dtq f1(U^k_p) correction term folded in
+  double s22[8][9];               // dt * S22[q][q0 + t] - [t == q - q0] dtq: likewise for f2
+  const double *F1new_p;          // coarse F at node p of the new sweep, NV comps
   const double *F1old[5];            // old coarse F at every coarse node
   const double *F2old[9];            // old fine F at the group's nodes, ns comps
   double *F2new[9];                  // new fine F at the group's nodes
@@ -177,5 +191,6 @@ struct FineChain {
 void launch_fine_chain(const DevState &s, const double *U0, double *U, const FineChain &fc,
                        cudaStream_t st);
 void launch_chem_only(const DevState &s, const double *U, double *F2, cudaStream_t st);
+void launch_exp(const Mech *m, const double *x, double *y, long long n, cudaStream_t st);
 
 }  // namespace smc

@@ -27,13 +27,14 @@ STATUS_NAMES = {0: "SMC_OK", 1: "SMC_ERR_ARG", 2: "SMC_ERR_CUDA", 3: "SMC_ERR_OO
 
 OPT = dict(precision=0, m47=1, m48=2, diffusion_mode=3, ref_species=4, xi_ratio=5,
            newton_tol=6, newton_maxit=7, t_guess=8, reactions=9, segment=10, profile=11,
-           use_graphs=12, x_layout=13)
+           use_graphs=12, x_layout=13, march=14, rates=15,
+           fine_repeat=16)
 KERNELS = ["prim", "grad", "march", "final", "update", "fine", "chem", "other"]
 
 EXPORTS = ["smc_create", "smc_destroy", "smc_rhs", "smc_sdc_step", "smc_prim_to_cons", "smc_autotune",
            "smc_set_stream", "smc_set_option", "smc_get_stats", "smc_synchronize",
            "smc_invalidate", "smc_collocation", "smc_multirate_collocation", "smc_rhs_noalloc",
-           "smc_last_error"]
+           "smc_exp", "smc_last_error"]
 
 
 class smc_grid(C.Structure):
@@ -79,9 +80,11 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
     lib.smc_get_stats.argtypes = [vp, C.POINTER(smc_stats)]
     lib.smc_synchronize.argtypes = [vp]
     lib.smc_invalidate.argtypes = [vp]
-    lib.smc_autotune.argtypes = [vp, vp, C.POINTER(C.c_int), C.POINTER(C.c_int)]
+    lib.smc_autotune.argtypes = [vp, vp, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]
     lib.smc_collocation.argtypes = [C.c_int, vp, vp]
-    lib.smc_multirate_collocation.argtypes = [C.c_int, C.c_int, vp, vp, vp, vp]
+    lib.smc_multirate_collocation.argtypes = [C.c_int, C.c_int, C.c_int, vp, vp, vp, vp]
+    lib.smc_exp.argtypes = [vp, vp, C.c_longlong]
+    lib.smc_exp.restype = C.c_int
     lib.smc_rhs_noalloc.argtypes = [C.POINTER(C.c_int), C.POINTER(C.c_double),
                                     C.POINTER(smc_mechanism), vp, vp, vp]
     lib.smc_last_error.argtypes = [vp]
@@ -133,16 +136,25 @@ def smc_collocation(nodes: int):
     return tau, S
 
 
-def smc_multirate_collocation(coarse: int, fine: int):
+def smc_multirate_collocation(coarse: int, fine: int, repeat: int = 1):
     """(t1, t2, S21, S22) of smc_multirate_collocation as NumPy arrays."""
-    M2 = (coarse - 1) * (fine - 1)
+    M2 = (coarse - 1) * (fine - 1) * max(repeat, 1)
     t1, t2 = np.zeros(coarse), np.zeros(M2 + 1)
     S21, S22 = np.zeros((M2, coarse)), np.zeros((M2, M2 + 1))
-    st = lib().smc_multirate_collocation(coarse, fine, *(C.c_void_p(a.ctypes.data)
-                                                          for a in (t1, t2, S21, S22)))
+    st = lib().smc_multirate_collocation(coarse, fine, repeat,
+                                         *(C.c_void_p(a.ctypes.data) for a in (t1, t2, S21, S22)))
     if st != SMC_OK:
         raise SmcError(st, "smc_multirate_collocation")
     return t1, t2, S21, S22
+
+
+def smc_exp(x, y):
+    """y = exp(x) elementwise by the library's exponential (CUDA float64
+    tensors of equal size); synchronous."""
+    st = lib().smc_exp(_ptr(x), _ptr(y), C.c_longlong(x.numel()))
+    if st != SMC_OK:
+        raise SmcError(st, "smc_exp")
+    return y
 
 
 def smc_rhs_noalloc(n, dx, mech, U, dUdt, stream=None):
@@ -236,7 +248,8 @@ class Smc:
         self.ns = mech.ns
         self.nv = 5 + mech.ns
         self.ncells = grid.ncells
-        for k, v in (options or {}).items():
+        # precision first: the per-precision options (x_layout, march) apply to it
+        for k, v in sorted((options or {}).items(), key=lambda kv: kv[0] != "precision"):
             self.set_option(k, v)
 
     def _check(self, st):
@@ -266,10 +279,11 @@ class Smc:
         return out
 
     def autotune(self, U) -> dict:
-        """Pick the fastest stencil segment length and x-line layout at U."""
-        seg, xl = C.c_int(), C.c_int()
-        self._check(lib().smc_autotune(self.h, _ptr(U), C.byref(seg), C.byref(xl)))
-        return {"segment": seg.value, "x_layout": xl.value}
+        """Pick the fastest stencil segment length, x-line layout and line
+        kernel at U."""
+        seg, xl, mv = C.c_int(), C.c_int(), C.c_int()
+        self._check(lib().smc_autotune(self.h, _ptr(U), C.byref(seg), C.byref(xl), C.byref(mv)))
+        return {"segment": seg.value, "x_layout": xl.value, "march": mv.value}
 
     def synchronize(self):
         self._check(lib().smc_synchronize(self.h))

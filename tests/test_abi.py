@@ -73,10 +73,12 @@ def test_collocation_matches_oracle(lib, nodes):
     assert np.abs(S - sdc.s_matrix(sdc.gauss_lobatto(nodes))).max() < 1e-14
 
 
-@pytest.mark.parametrize("coarse,fine", [(3, 5), (3, 9), (5, 5), (3, 2), (5, 3)])
-def test_multirate_collocation_matches_oracle(lib, coarse, fine):
-    t1, t2, S21, S22 = smc.smc_multirate_collocation(coarse, fine)
-    a, b, S21o, S22o = sdc.mr_matrices(coarse, fine)
+@pytest.mark.parametrize("coarse,fine,repeat", [(3, 5, 1), (3, 9, 1), (5, 5, 1), (3, 2, 1),
+                                                (5, 3, 1), (3, 3, 8), (3, 5, 2), (5, 3, 3)])
+def test_multirate_collocation_matches_oracle(lib, coarse, fine, repeat):
+    """Type (b) (repeat 1) and type (c) fine nodes and matrices."""
+    t1, t2, S21, S22 = smc.smc_multirate_collocation(coarse, fine, repeat)
+    a, b, S21o, S22o = sdc.mr_matrices(coarse, fine, repeat)
     assert np.abs(t1 - a).max() < 1e-15
     assert np.abs(t2 - b).max() < 1e-15
     assert np.abs(S21 - S21o).max() < 1e-14
@@ -88,6 +90,8 @@ def test_collocation_rejects_bad_arguments(lib):
         smc.smc_collocation(1)
     with pytest.raises(smc.SmcError):
         smc.smc_multirate_collocation(3, 12)
+    with pytest.raises(smc.SmcError):
+        smc.smc_multirate_collocation(3, 3, 0)
 
 
 def test_create_rejects_bad_mechanism_without_touching_the_gpu(lib):

@@ -40,10 +40,12 @@ def gpu_rhs(S, grid, mech, U, **options):
         return F.cpu().numpy()
 
 
+@pytest.mark.parametrize("march", [0, 1])
 @pytest.mark.parametrize("mode", [0, 1])
-def test_mixed_rhs_c1(smc, mode):
+def test_mixed_rhs_c1(smc, mode, march):
+    """Both line kernels (per-face windows, sliding register windows)."""
     wl, U, U_g = state("c1", seed=1, p_amp=0.03)
-    got = gpu_rhs(smc, wl.grid, wl.mech, U, diffusion_mode=mode)
+    got = gpu_rhs(smc, wl.grid, wl.mech, U, diffusion_mode=mode, march=march)
     err = relerr(got, oracle_rhs(wl, U_g, mode="vc" if mode == 0 else "ref"))
     print("mixed c1 per-component error", np.array2string(err, precision=2))
     assert err.max() < TOL, err
@@ -65,12 +67,13 @@ def test_mixed_rhs_flame(smc):
     assert err.max() < TOL, err
 
 
-def test_mixed_rhs_multibox_21_species(smc):
+@pytest.mark.parametrize("march", [0, 1])
+def test_mixed_rhs_multibox_21_species(smc, march):
     wl = synth.workload("c4", seed=3, n=12)
     prim_g = synth.boxes_to_global(wl.grid, wl.prim)
     U_g = thermo.conserved(prim_g, wl.mech.nasa7, wl.mech.W)
     U = synth.global_to_boxes(wl.grid, U_g)
-    err = relerr(gpu_rhs(smc, wl.grid, wl.mech, U), oracle_rhs(wl, U_g))
+    err = relerr(gpu_rhs(smc, wl.grid, wl.mech, U, march=march), oracle_rhs(wl, U_g))
     print("mixed c4(8 boxes) per-component error", np.array2string(err, precision=2))
     assert err.max() < TOL, err
 
@@ -94,6 +97,62 @@ def test_mixed_sdc_step(smc):
     assert err.max() < TOL, err
     # the state itself is far more accurate
     assert relerr(U1, ref).max() < 1e-8
+
+
+@pytest.mark.parametrize("rates", [0, 1])
+def test_mixed_mrsdc_step_multibox(smc, rates):
+    """Mode-1 multirate step (3 coarse / 5 fine nodes, 4 sweeps) on 8 uneven
+    boxes with 21 species, FP64 rates or FP32-mantissa rates in the reaction
+    substeps: the increment within the mixed tolerance of the FP64 oracle."""
+    wl = synth.workload("c4", seed=2, n=10)
+    prim_g = synth.boxes_to_global(wl.grid, wl.prim)
+    U_g = thermo.conserved(prim_g, wl.mech.nasa7, wl.mech.W)
+    U = synth.global_to_boxes(wl.grid, U_g)
+    with smc.Smc(wl.grid, wl.mech, {"precision": 1, "rates": rates}) as h:
+        Ud = dev(U)
+        h.sdc_step(Ud, wl.dt, nodes=3, sweeps=4, reaction_substeps=5)
+        h.synchronize()
+        U1 = Ud.cpu().numpy()
+    from oracle import rhs as orhs
+
+    def part(which):
+        def f(u, t=0.0):
+            tr, ch = orhs.rhs_periodic(u, wl.mech, wl.grid.dx, parts=True)
+            return tr if which == "transport" else ch
+        return f
+    ref, _, _, _, _ = osdc.mrsdc_step(U_g, part("transport"), part("chem"), wl.dt,
+                                      coarse=3, fine=5, sweeps=4)
+    ref = synth.global_to_boxes(wl.grid, ref)
+    err = relerr(U1 - U, ref - U)
+    print("mixed MRSDC increment error", np.array2string(err, precision=2))
+    assert err.max() < TOL, err
+
+
+@pytest.mark.parametrize("rates", [0, 1])
+@pytest.mark.parametrize("name,n", [("c3", 16), ("c4", 10)])
+def test_mixed_rates_match_fp64_rates(smc, name, n, rates):
+    """The mixed path's production rates alone (its full right-hand side
+    minus its reaction-free one, which share every transport operation),
+    FP64 or with FP32 mantissas: against the oracle's rates, per species, on
+    the 300-2000 K flame field and on the 21-species mechanism.  FP64 rates
+    at the temperature of the float-pair primitives agree to ~1e-12; FP32
+    mantissas within the mixed tolerance."""
+    if name == "c4":
+        wl = synth.workload("c4", seed=4, n=n)
+        prim_g = synth.boxes_to_global(wl.grid, wl.prim)
+        U_g = thermo.conserved(prim_g, wl.mech.nasa7, wl.mech.W)
+        U = synth.global_to_boxes(wl.grid, U_g)
+    else:
+        wl, U, U_g = state(name, seed=2, n=n)
+    full = gpu_rhs(smc, wl.grid, wl.mech, U, rates=rates)
+    noreact = gpu_rhs(smc, wl.grid, wl.mech, U, reactions=0, rates=rates)
+    from oracle import rhs as orhs
+    _, ch = orhs.rhs_periodic(U_g, wl.mech, wl.grid.dx, parts=True)
+    ch = synth.global_to_boxes(wl.grid, ch)
+    assert np.array_equal(full[:5], noreact[:5])
+    err = relerr(full[5:] - noreact[5:], ch[5:])
+    print(f"mixed rates error ({name}, rates={rates})", np.array2string(err, precision=2))
+    assert err.max() < (TOL if rates else 1e-9), err
 
 
 def test_mixed_keeps_eighth_order_to_the_fp32_floor(smc):

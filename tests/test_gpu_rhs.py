@@ -12,6 +12,7 @@ from util import oracle_rhs, relerr, state
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
+TOL_MIXED = 1e-5
 TOL = 1e-12
 
 
@@ -203,18 +204,29 @@ def test_bad_arguments(smc):
 @pytest.mark.parametrize("precision", [0, 1])
 def test_tile_choices_give_identical_results_and_autotune(smc, precision):
     """Segment length and x-line layout change only the schedule: every
-    choice gives the same bits; the autotuner picks one of them."""
+    choice gives the same bits for a given line kernel; the two mixed line
+    kernels agree to the mixed tolerance; the autotuner picks one of the
+    choices."""
     wl, U, U_g = state("c1", seed=7, p_amp=0.03)
-    outs = []
-    for seg in (8, 16, 64):
-        for xl in (0, 1):
-            outs.append(gpu_rhs(smc, wl, U, precision=precision, segment=seg, x_layout=xl))
-    for o in outs[1:]:
-        assert np.array_equal(o, outs[0])
+    marches = (0, 1) if precision else (0,)
+    ref = {}
+    for mv in marches:
+        outs = []
+        for seg in (8, 16, 64):
+            for xl in (0, 1):
+                outs.append(gpu_rhs(smc, wl, U, precision=precision, segment=seg, x_layout=xl,
+                                    march=mv))
+        for o in outs[1:]:
+            assert np.array_equal(o, outs[0])
+        ref[mv] = outs[0]
+    if precision:
+        assert relerr(ref[1], oracle_rhs(wl, U_g)).max() < TOL_MIXED
+        assert relerr(ref[1], ref[0]).max() < TOL_MIXED
     with smc.Smc(wl.grid, wl.mech, {"precision": precision}) as h:
         choice = h.autotune(dev(U))
         assert choice["segment"] in (8, 16, 32, 64) and choice["x_layout"] in (0, 1)
+        assert choice["march"] in marches
         F = torch.empty_like(dev(U))
         h.rhs(dev(U), F)
         h.synchronize()
-    assert np.array_equal(F.cpu().numpy(), outs[0])
+    assert np.array_equal(F.cpu().numpy(), ref[choice["march"]])

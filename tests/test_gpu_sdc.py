@@ -148,3 +148,57 @@ def test_graph_replay_matches_eager_launches(smc, rsub):
             out.append((Ud.cpu().numpy(), st["n_rhs"], st["n_react"], st["launches"]))
     assert np.array_equal(out[0][0], out[1][0])
     assert out[0][1:] == out[1][1:]
+
+
+@pytest.mark.parametrize("fine,repeat", [(3, 2), (5, 2)])
+def test_mrsdc_type_c_step_multibox(smc, fine, repeat):
+    """Type (c) fine nodes: `repeat` groups of `fine` Gauss-Lobatto nodes in
+    every coarse interval (3 coarse nodes, 4 sweeps), 8 uneven boxes, 21
+    species, against the oracle's type (c) step and its evaluation counts."""
+    wl = synth.workload("c4", seed=5, n=10)
+    from oracle import thermo
+    prim_g = synth.boxes_to_global(wl.grid, wl.prim)
+    U_g = thermo.conserved(prim_g, wl.mech.nasa7, wl.mech.W)
+    U = synth.global_to_boxes(wl.grid, U_g)
+    with smc.Smc(wl.grid, wl.mech, {"fine_repeat": repeat}) as h:
+        Ud = dev(U)
+        h.sdc_step(Ud, wl.dt, nodes=3, sweeps=4, reaction_substeps=fine)
+        h.synchronize()
+        st = h.stats()
+        U1 = Ud.cpu().numpy()
+    ref, _, _, n1, n2 = osdc.mrsdc_step(U_g, oracle_f(wl, "transport"), oracle_f(wl, "chem"),
+                                        wl.dt, coarse=3, fine=fine, repeat=repeat, sweeps=4)
+    ref = synth.global_to_boxes(wl.grid, ref)
+    M2 = 2 * (fine - 1) * repeat
+    assert (st["n_rhs"], st["n_react"]) == (n1, n2) == (4 * 2 + 1, 4 * M2 + 1)
+    err = relerr(U1 - U, ref - U)
+    assert err.max() < TOL, err
+
+
+def test_eval_counts_reproduce_table_mrsdc_runtime(smc):
+    """The advection-diffusion / reaction evaluation counts of the paper's
+    multirate run table (to t = 4.2e-7 s, 4 sweeps, 3 coarse nodes), counted
+    by the library over the same number of steps, for every row the library
+    supports (fine groups of up to 9 nodes; the 13-node row is outside)."""
+    import os
+    rows = [l.split() for l in open(os.path.join(os.path.dirname(__file__), "golden",
+                                                 "mrsdc_runtime_evals.txt"))
+            if l.strip() and not l.startswith("#")]
+    wl, U, _ = state("c1", seed=6)
+    checked = 0
+    for dt_ns, fine, repeat, n_ad, n_r in [tuple(int(v) for v in r) for r in rows]:
+        if fine > 9:
+            continue
+        steps = round(420 / dt_ns)
+        with smc.Smc(wl.grid, wl.mech, {"fine_repeat": repeat}) as h:
+            Ud = dev(U)
+            for _ in range(steps):
+                h.sdc_step(Ud, wl.dt * 0.1, nodes=3, sweeps=4, reaction_substeps=fine)
+            h.synchronize()
+            st = h.stats()
+        if fine == 0:
+            assert (st["n_rhs"], st["n_rhs"]) == (n_ad, n_r)
+        else:
+            assert (st["n_rhs"], st["n_react"]) == (n_ad, n_r)
+        checked += 1
+    assert checked == 4
