@@ -154,26 +154,33 @@ def march_flops_per_cell_mixed(ns: int, mode: int = 0) -> float:
     return face + diffs + conv + vc + 5 + ns
 
 
-def chem_flops_per_eval(ns: int, nr: int, mol_sides: float = 4.0) -> float:
-    """FP64 flops of one production-rate evaluation per cell, counted from the
-    source (FMA = 2; the table-driven exponential = 20 flops, log = 20): per
-    reaction 43 (exponent 8, exponential 20, products and net rate ~7,
-    species updates 8), per species 49 (Gibbs energy 23, z_k with its
-    exponential 23, sums 3), 31 per cell (ln T, 1/T, pressure powers)."""
-    return 43.0 * nr + 49.0 * ns + 31.0
+def chem_flops_per_eval(ns: int, nr: int) -> float:
+    """FP64 flops of one reaction-term evaluation per cell (FMA = 2), counted
+    from the source: per reaction 34 (exponent 7.6, concentration products
+    2.5, table-driven exponential 14, net rate 3, species updates 7.2), per
+    species 43 (Gibbs energy 12, shift 2, z_k with its exponential 15,
+    mixture polynomial of the Newton solve 14), per cell 210 (ln T, 1/T,
+    the pressure powers, 1/rho, velocities, the Newton iterations).
+    Cross-checked with ncu's DFMA/DMUL/DADD counts of k_fine_chain (4132 per
+    evaluation at 21 species / 84 reactions against 3969 counted)."""
+    return 34.0 * nr + 43.0 * ns + 210.0
+
+
+def chem_flops_per_eval_rates32(ns: int, nr: int) -> float:
+    """FP64 flops of the same evaluation with FP32-mantissa rates: per
+    reaction the exponent (7.6) and its argument reduction (5), per species
+    the Gibbs energy, shift and reduction (19) and the Newton mixture
+    polynomial (14), per cell 200.  ncu: 2004 per evaluation against 1951."""
+    return 12.6 * nr + 33.0 * ns + 200.0
 
 
 def fine_flops_per_substep(ns: int, nr: int, M1: int, Y: int, rates32: bool = False) -> float:
-    """FP64 flops of one fine substep of the multirate chain per cell: the
-    reaction evaluation, the temperature Newton solve (mixture-polynomial
-    setup 13 ns, ~5 iterations of 22) and the update of eq. mrupdate
-    (NV (2 + 2 (M1 + 1)) + ns (2 + 2 Y)).  With FP32-mantissa rates only their
-    FP64 part counts: per reaction the exponent (8) and the argument
-    reduction (5), per species the Gibbs energy (23) and its reduction (7)."""
+    """FP64 flops of one fine substep of the multirate chain per cell: one
+    reaction-term evaluation (Newton solve included) and the update of
+    eq. mrupdate, NV (2 + 2 (M1 + 1)) + ns (2 + 2 Y)."""
     nv = 5 + ns
-    chem = (13.0 * nr + 30.0 * ns + 31.0) if rates32 else chem_flops_per_eval(ns, nr)
-    return (chem + 13.0 * ns + 5 * 22 + 12
-            + nv * (2 + 2 * (M1 + 1)) + ns * (2 + 2 * Y))
+    chem = chem_flops_per_eval_rates32(ns, nr) if rates32 else chem_flops_per_eval(ns, nr)
+    return chem + nv * (2 + 2 * (M1 + 1)) + ns * (2 + 2 * Y)
 
 
 PRECISION_TEXT = {

@@ -133,10 +133,17 @@ enum {
                                   FP64 like the FP64 path; 1 FP32 mantissas after FP64 Gibbs
                                   energies, reaction exponents and exponent reductions
                                   (about 1e-6 relative; ignored in FP64 precision) */
-  SMC_OPT_FINE_REPEAT = 16     /* multirate fine nodes (Sec. 3.2): each coarse interval holds
+  SMC_OPT_FINE_REPEAT = 16,    /* multirate fine nodes (Sec. 3.2): each coarse interval holds
                                   this many consecutive groups of reaction_substeps
                                   Gauss-Lobatto nodes; 1 (default) is type (b), more is
                                   type (c) (1..8; at most 64 fine intervals per step) */
+  SMC_OPT_SDC_EXIT = 17        /* eps >= 0; 0 (default) runs every sweep.  eps > 0: after each
+                                  sweep compute the residual R^k = U_0 + dt q.F^k - U_M^k of
+                                  eq. residual (for MRSDC the coarse and fine quadratures of
+                                  f1 and f2) and end the step once |R^(k-1)| / |R^k| < 1 + eps
+                                  or |R^k| = 0.  Reads the residual to the host every sweep
+                                  (a stream synchronisation); steps are then launched one
+                                  kernel at a time, not replayed as a graph */
 };
 
 /* Kernel classes counted in smc_stats (launches always; times only while
@@ -163,6 +170,10 @@ typedef struct {
   long long device_bytes;    /* device memory held by the handle */
   long long launches[SMC_NKERNELS];   /* kernel launches per class */
   double kernel_ms[SMC_NKERNELS];     /* summed device time per class (profiling on) */
+  int sweeps_done;           /* sweeps of the last smc_sdc_step */
+  double residual[64];       /* |R^k| after sweep k of the last step (SMC_OPT_SDC_EXIT > 0
+                                only; 0 otherwise): max over components of
+                                max|R_c| / max|U_0,c| */
 } smc_stats;
 
 /* Create a handle: validates the mechanism (limits above) and the grid,
@@ -260,6 +271,22 @@ smc_status smc_multirate_collocation(int coarse, int fine, int repeat, double *t
  * the GPU race and must be serialised by the caller. */
 smc_status smc_rhs_noalloc(const int n[3], const double dx[3], const smc_mechanism *mech,
                            const double *U, double *dUdt, void *stream);
+
+/* The appendix heat-equation problems (App. A, T1/T2):
+ *   u_t = (a u_x)_x + (b u_y)_y + exp(-t) G(x, y)
+ * on a periodic N x N grid of spacing h (N >= 8), both terms by the narrow
+ * stencil of Sec. 2.2 with free parameters m47, m48, advanced by nsteps
+ * SDC steps (Sec. 3.1: `nodes` Gauss-Lobatto nodes, `sweeps` sweeps) of dt
+ * from t0.  a, b, G (may be NULL: no source) and u are caller-owned device
+ * arrays of N*N doubles, row-major with x fastest; u is advanced in place.
+ * The step recycles f(U_M) as the next f(U_0).  *n_evals (may be NULL)
+ * receives the number of operator evaluations.  Allocates its scratch
+ * ((2 + 2 (nodes - 1)) N^2 doubles) and synchronises `stream` (a
+ * cudaStream_t, NULL = default) before returning.  SMC_ERR_ARG for bad
+ * sizes or host pointers, SMC_ERR_OOM, SMC_ERR_CUDA. */
+smc_status smc_heat2d(int N, double h, const double *a, const double *b, const double *G,
+                      double m47, double m48, double t0, double dt, int nsteps, int nodes,
+                      int sweeps, double *u, long long *n_evals, void *stream);
 
 /* The exponential used by the production rates (a table-driven method, not
  * the paper's: Sec. 2.1 only needs exp), applied elementwise y[i] = exp(x[i])

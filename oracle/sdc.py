@@ -102,6 +102,59 @@ def sdc_residual(U0, Unodes_last, F, dt, nodes):
     return U0 + dt * sum(q[j] * F[j] for j in range(nodes)) - Unodes_last
 
 
+def residual_norm(R, U0) -> float:
+    """|R| = max over components c of max|R_c| / max|U0_c| (the paper gives
+    no norm; this reading is scale-free per component).  Arrays [nv, ...]."""
+    R = np.abs(np.asarray(R)).reshape(np.shape(R)[0], -1).max(axis=1)
+    S = np.abs(np.asarray(U0)).reshape(np.shape(U0)[0], -1).max(axis=1)
+    return float(np.max(np.where(S > 0, R / np.where(S > 0, S, 1.0), R)))
+
+
+def stop_rule(hist, eps: float) -> bool:
+    """End the step once |R^(k-1)| / |R^k| < 1 + eps (the successive
+    residuals no longer shrink) or |R^k| = 0."""
+    if hist[-1] == 0.0:
+        return True
+    return len(hist) > 1 and hist[-2] / hist[-1] < 1.0 + eps
+
+
+def sdc_step_exit(U0, f, dt: float, nodes: int = 3, max_sweeps: int = 8, eps: float = 0.5,
+                  F0=None, t0: float = 0.0):
+    """sdc_step with the residual early exit of Sec. 3.1: after every sweep
+    compute |R^k| (eq. residual) and stop by stop_rule.  Returns (U_new,
+    f(U_new), evaluations, residual history)."""
+    tau = gauss_lobatto(nodes)
+    M = nodes - 1
+    S = s_matrix(tau)
+    q = q_matrix(tau)[-1]
+    dtm = dt * np.diff(tau)
+    nev = 0
+    if F0 is None:
+        F0 = f(U0, t0)
+        nev += 1
+    tm = t0 + dt * tau
+    Fold = [F0] * (M + 1)
+    U = U0
+    hist = []
+    for _ in range(max_sweeps):
+        Fnew = [F0] + [None] * M
+        U = U0
+        for m in range(M):
+            if m > 0:
+                Fnew[m] = f(U, tm[m])
+                nev += 1
+            SF = sum(S[m, j] * Fold[j] for j in range(M + 1))
+            U = U + dtm[m] * (Fnew[m] - Fold[m]) + dt * SF
+        Fnew[M] = f(U, tm[M])
+        nev += 1
+        Fold = Fnew
+        R = U0 + dt * sum(q[j] * Fold[j] for j in range(M + 1)) - U
+        hist.append(residual_norm(R, U0))
+        if stop_rule(hist, eps):
+            break
+    return U, Fold[M], nev, hist
+
+
 # ---------------------------------------------------------------- multirate
 
 def mr_nodes(coarse: int, fine: int, repeat: int = 1):
@@ -142,9 +195,15 @@ def mr_matrices(coarse: int, fine: int, repeat: int = 1):
 
 
 def mrsdc_step(U0, f1, f2, dt: float, coarse: int = 3, fine: int = 5, repeat: int = 1,
-               sweeps: int = 4, F10=None, F20=None):
+               sweeps: int = 4, F10=None, F20=None, eps: float = 0.0, history=None):
     """One mode-1 MRSDC step (eq. mrupdate).  f1: slow (advection-diffusion),
-    f2: fast (reactions).  Returns (U_new, f1(U_new), f2(U_new), n_f1, n_f2)."""
+    f2: fast (reactions).  Returns (U_new, f1(U_new), f2(U_new), n_f1, n_f2).
+
+    eps > 0: after every sweep the residual U_0 + dt (q1 . F1 + q2 . F2) - U_M
+    (eq. residual with the coarse and the fine quadrature, q1 and q2 the
+    column sums of S21 and S22) is appended to `history` (a list) and the
+    step ends by stop_rule.  f2 returns full-size arrays (zero outside the
+    species components)."""
     t1, t2, S21, S22 = mr_matrices(coarse, fine, repeat)
     M1, M2 = coarse - 1, t2.shape[0] - 1
     per = M2 // M1                       # fine intervals per coarse interval
@@ -180,4 +239,12 @@ def mrsdc_step(U0, f1, f2, dt: float, coarse: int = 3, fine: int = 5, repeat: in
         n1 += 1
         n2 += 1
         F1old, F2old = F1new, F2new
+        if eps > 0.0:
+            q1 = S21.sum(axis=0)
+            q2 = S22.sum(axis=0)
+            R = (U0 + dt * sum(q1[j] * F1old[j] for j in range(M1 + 1))
+                 + dt * sum(q2[t] * F2old[t] for t in range(M2 + 1)) - U)
+            history.append(residual_norm(R, U0))
+            if stop_rule(history, eps):
+                break
     return U, F1old[M1], F2old[M2], n1, n2

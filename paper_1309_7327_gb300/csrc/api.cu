@@ -28,6 +28,11 @@ struct smc_handle {
   int march[2] = {0, 1};                // stencil-line kernel (FP64, mixed)
   int rates32 = 0;                      // FP32-mantissa production rates (mixed only)
   int fine_repeat = 1;                  // groups of fine nodes per coarse interval (type (c) if > 1)
+  double sdc_exit = 0.0;                // residual early exit threshold (0: off)
+  int sweeps_done = 0;
+  double resid[64] = {};
+  ResidualTable *d_restab = nullptr;
+  unsigned long long *d_resout = nullptr;
   cudaStream_t stream = 0;
   int device = 0;
 
@@ -181,41 +186,8 @@ DevState state(smc_handle *h) {
 }
 
 void build_coef(smc_handle *h) {
-  // 8th-order narrow-stencil matrix M (Sec. 2.2), rows m = -3..4, cols n = -3..4
-  const double a = h->m47, b = h->m48;
-  double m[5][9] = {};
-  m[1][1] = 5.0 / 336 + b;
-  m[1][2] = -83.0 / 3600 - a / 5 - 14.0 * b / 5;
-  m[1][3] = 299.0 / 50400 + 2.0 * a / 5 + 13.0 * b / 5;
-  m[1][4] = 17.0 / 12600 - a / 5 - 4.0 * b / 5;
-  m[1][5] = 1.0 / 1120;
-  m[2][1] = -11.0 / 560 - 2 * b;
-  m[2][2] = -31.0 / 360 + a + 3 * b;
-  m[2][3] = 41.0 / 200 - 9.0 * a / 5 + 4.0 * b / 5;
-  m[2][4] = -5927.0 / 50400 + 4.0 * a / 5 - 9.0 * b / 5;
-  m[2][5] = 17.0 / 600 - a / 5 - 4.0 * b / 5;
-  m[2][6] = -503.0 / 50400 + a / 5 + 4.0 * b / 5;
-  m[3][1] = -1.0 / 280;
-  m[3][2] = 1097.0 / 5040 - 2 * a + 6 * b;
-  m[3][3] = -1349.0 / 10080 + 3 * a - 12 * b;
-  m[3][4] = -887.0 / 5040 - a + 6 * b;
-  m[3][5] = 3613.0 / 50400 + 4.0 * a / 5 - 9.0 * b / 5;
-  m[3][6] = 467.0 / 25200 - 3.0 * a / 5 + 18.0 * b / 5;
-  m[3][7] = 139.0 / 25200 - a / 5 - 9.0 * b / 5;
-  m[4][1] = 17.0 / 1680 + 2 * b;
-  m[4][2] = -319.0 / 2520 + 2 * a - 8 * b;
-  m[4][3] = -919.0 / 5040 - 2 * a + 6 * b;
-  m[4][4] = -445.0 / 2016;
-  m[4][5] = 583.0 / 720 - a + 6 * b;
-  m[4][6] = -65.0 / 224 - 7 * b;
-  m[4][7] = a;
-  m[4][8] = b;
-  double M[8][8] = {};
-  for (int r = 0; r < 4; ++r)
-    for (int c = 0; c < 8; ++c) {
-      M[r][c] = m[r + 1][c + 1];
-      M[7 - r][7 - c] = -m[r + 1][c + 1];
-    }
+  double M[8][8];
+  narrow8_matrix(h->m47, h->m48, M);
   const double D8[4] = {4.0 / 5, -1.0 / 5, 4.0 / 105, -1.0 / 280};
   for (int d = 0; d < 3; ++d) {
     const double ih2 = 1.0 / (h->dx[d] * h->dx[d]);
@@ -394,6 +366,45 @@ smc_status eval_rhs(smc_handle *h, const double *U, double *F, int transport, in
   return SMC_OK;
 }
 
+// |R| of eq. residual after a sweep: max over components of
+// max|R_c| / max|U_0,c|, read back to the host (synchronises the stream).
+smc_status sweep_residual(smc_handle *h, const double *U0, const double *UM,
+                          const ResidualTable &tab, double &norm) {
+  if (!h->d_restab) {
+    CUDA_TRY(h, dalloc(h, &h->d_restab, 1));
+    CUDA_TRY(h, dalloc(h, &h->d_resout, 2 * (size_t)h->nv));
+  }
+  CUDA_TRY(h, cudaMemcpyAsync(h->d_restab, &tab, sizeof(ResidualTable), cudaMemcpyHostToDevice,
+                              h->stream));
+  CUDA_TRY(h, cudaMemsetAsync(h->d_resout, 0, 2 * (size_t)h->nv * sizeof(unsigned long long),
+                              h->stream));
+  {
+    Timed t(h, SMC_K_UPDATE);
+    launch_residual(U0, UM, h->d_restab, h->nv, h->ncells, h->d_resout, h->stream);
+  }
+  CUDA_TRY(h, cudaGetLastError());
+  std::vector<unsigned long long> o(2 * (size_t)h->nv);
+  CUDA_TRY(h, cudaMemcpyAsync(o.data(), h->d_resout, o.size() * sizeof(unsigned long long),
+                              cudaMemcpyDeviceToHost, h->stream));
+  CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  norm = 0.0;
+  for (int c = 0; c < h->nv; ++c) {
+    double r, u;
+    memcpy(&r, &o[c], sizeof(double));
+    memcpy(&u, &o[h->nv + c], sizeof(double));
+    norm = std::max(norm, u > 0.0 ? r / u : r);
+  }
+  return SMC_OK;
+}
+
+// Record |R^k| after sweep k; true when the step should end here.
+bool residual_says_stop(smc_handle *h, int k, double r) {
+  if (k < 64) h->resid[k] = r;
+  h->sweeps_done = k + 1;
+  if (r == 0.0) return true;
+  return k > 0 && k < 64 && h->resid[k - 1] / r < 1.0 + h->sdc_exit;
+}
+
 smc_status sdc_single_rate(smc_handle *h, double *U, const void *key, double dt, int nodes, int sweeps) {
   const int M = nodes - 1;
   std::vector<double> tau, S;
@@ -447,6 +458,22 @@ smc_status sdc_single_rate(smc_handle *h, double *U, const void *key, double dt,
     h->n_rhs++;
     fold = fnew;
     set ^= 1;
+    h->sweeps_done = k + 1;
+    if (h->sdc_exit > 0.0) {
+      // eq. residual with q the last row of Q: q_j = sum_m S_mj
+      ResidualTable tab;
+      memset(&tab, 0, sizeof(tab));
+      tab.n1 = M + 1;
+      for (int j = 0; j <= M; ++j) {
+        double q = 0.0;
+        for (int m = 0; m < M; ++m) q += S[m * (M + 1) + j];
+        tab.c1[j] = dt * q;
+        tab.src1[j] = h->fpool[fnew[j]];
+      }
+      double r;
+      if ((st = sweep_residual(h, h->d_U0, U, tab, r))) return st;
+      if (residual_says_stop(h, k, r)) break;
+    }
   }
   // keep f(U_M) in slot 0 so that every recycled step issues the same
   // launches on the same buffers (the step can then be replayed as a graph)
@@ -543,6 +570,30 @@ smc_status sdc_multirate(smc_handle *h, double *U, const void *key, double dt, i
     f1old = f1new;
     f2old = f2new;
     set ^= 1;
+    h->sweeps_done = k + 1;
+    if (h->sdc_exit > 0.0) {
+      // eq. residual with the coarse quadrature of f1 and the fine one of f2:
+      // q1_j = sum_q S21_qj, q2_t = sum_q S22_qt
+      ResidualTable tab;
+      memset(&tab, 0, sizeof(tab));
+      tab.n1 = M1 + 1;
+      tab.n2 = M2 + 1;
+      for (int j = 0; j <= M1; ++j) {
+        double q = 0.0;
+        for (int qq = 0; qq < M2; ++qq) q += S21[qq * (M1 + 1) + j];
+        tab.c1[j] = dt * q;
+        tab.src1[j] = h->fpool[f1new[j]];
+      }
+      for (int t = 0; t <= M2; ++t) {
+        double q = 0.0;
+        for (int qq = 0; qq < M2; ++qq) q += S22[qq * (M2 + 1) + t];
+        tab.c2[t] = dt * q;
+        tab.src2[t] = h->rpool[f2new[t]];
+      }
+      double r;
+      if ((st = sweep_residual(h, h->d_U0, U, tab, r))) return st;
+      if (residual_says_stop(h, k, r)) break;
+    }
   }
   if (f1old[M1] != 0)
     CUDA_TRY(h, cudaMemcpyAsync(h->fpool[0], h->fpool[f1old[M1]], n * sizeof(double),
@@ -727,6 +778,8 @@ smc_status smc_destroy(smc_handle *h) {
   for (double *p : h->rpool) cudaFree(p);
   cudaFree(h->d_U0);
   cudaFree(h->d_dUf);
+  cudaFree(h->d_restab);
+  cudaFree(h->d_resout);
   for (int i = 0; i < 3; ++i) cudaFree(h->d_stage[i]);
   drop_graph(h);
   for (auto &p : h->ev_pending) {
@@ -769,6 +822,8 @@ namespace {
 
 smc_status step_body(smc_handle *h, double *Ud, const void *key, double dt, int nodes, int sweeps,
                      int rsub) {
+  h->sweeps_done = 0;
+  for (double &r : h->resid) r = 0.0;
   return rsub <= 1 ? sdc_single_rate(h, Ud, key, dt, nodes, sweeps)
                    : sdc_multirate(h, Ud, key, dt, nodes, sweeps, rsub);
 }
@@ -860,7 +915,7 @@ smc_status smc_sdc_step(smc_handle *h, double *U, double dt, int nodes, int swee
   const bool recycled = h->cache_U == (const double *)U && h->cache_f == 0 &&
                         h->cache_kind == (reaction_substeps <= 1 ? 1 : 2);
   // profiling times every launch with its own events: launch eagerly then
-  if (recycled && h->use_graphs && h->stream != 0 && !h->profile)
+  if (recycled && h->use_graphs && h->stream != 0 && !h->profile && h->sdc_exit == 0.0)
     st = graph_step(h, Ud, U, dt, nodes, sweeps, reaction_substeps);
   else
     st = step_body(h, Ud, U, dt, nodes, sweeps, reaction_substeps);
@@ -952,6 +1007,10 @@ smc_status smc_set_option(smc_handle *h, int key, double v) {
       if (v < 1 || v > 8 || v != floor(v)) return fail(h, SMC_ERR_ARG, "fine repeat must be 1..8");
       h->fine_repeat = (int)v;
       return SMC_OK;
+    case SMC_OPT_SDC_EXIT:
+      if (!(v >= 0.0) || !std::isfinite(v)) return fail(h, SMC_ERR_ARG, "sdc exit must be >= 0");
+      h->sdc_exit = v;
+      return SMC_OK;
     case SMC_OPT_RATES:
       if (v != 0.0 && v != 1.0) return fail(h, SMC_ERR_ARG, "rates must be 0 or 1");
       h->rates32 = (int)v;
@@ -989,6 +1048,8 @@ smc_status smc_get_stats(smc_handle *h, smc_stats *o) {
     o->launches[k] = h->launches[k];
     o->kernel_ms[k] = h->kernel_ms[k];
   }
+  o->sweeps_done = h->sweeps_done;
+  for (int k = 0; k < 64; ++k) o->residual[k] = h->sdc_exit > 0.0 ? h->resid[k] : 0.0;
   return SMC_OK;
 }
 

@@ -186,6 +186,63 @@ void launch_transpose_x(const DevState &s, const void *src, void *dst, int plane
                                                  (const float *)src, (float *)dst, planes);
 }
 
+// Collocation residual of eq. residual, R = U_0 - U_M + sum_j c1_j F1_j (all
+// components) + sum_t c2_t F2_t (species components, F2 arrays hold ns
+// components), reduced per component to max|R| (out[c]) and max|U_0|
+// (out[nv + c]).  Non-negative doubles order like their bit patterns, so the
+// maxima reduce with integer atomicMax; out must be zeroed before the launch.
+__global__ void __launch_bounds__(256) k_residual(const double *__restrict__ U0,
+                                                  const double *__restrict__ UM,
+                                                  const ResidualTable *__restrict__ tab, int nv,
+                                                  long long NI,
+                                                  unsigned long long *__restrict__ out) {
+  const long long n = (long long)nv * NI;
+  const int n1 = tab->n1, n2 = tab->n2;
+  for (long long base = (long long)blockIdx.x * blockDim.x; base < n;
+       base += (long long)gridDim.x * blockDim.x) {
+    const long long i = base + threadIdx.x;
+    double r = 0.0, u = 0.0;
+    int c = -1;
+    if (i < n) {
+      c = (int)(i / NI);
+      r = U0[i] - UM[i];
+      for (int j = 0; j < n1; ++j) r = fma(tab->c1[j], tab->src1[j][i], r);
+      if (c >= 5)
+        for (int t = 0; t < n2; ++t) r = fma(tab->c2[t], tab->src2[t][i - 5 * NI], r);
+      r = fabs(r);
+      u = fabs(U0[i]);
+    }
+    // one atomic per component present in the warp (a warp spans at most
+    // two components when NI >= 32)
+    const unsigned mask = 0xffffffffu;
+    const int c0 = __shfl_sync(mask, c, 0);
+    for (int cc = c0; cc >= 0; ) {
+      double rr = (c == cc) ? r : 0.0, uu = (c == cc) ? u : 0.0;
+      for (int off = 16; off; off >>= 1) {
+        rr = fmax(rr, __shfl_xor_sync(mask, rr, off));
+        uu = fmax(uu, __shfl_xor_sync(mask, uu, off));
+      }
+      if ((threadIdx.x & 31) == 0) {
+        atomicMax(out + cc, (unsigned long long)__double_as_longlong(rr));
+        atomicMax(out + nv + cc, (unsigned long long)__double_as_longlong(uu));
+      }
+      // the next component present in this warp, if any
+      const int nxt = (c > cc) ? c : 0x7fffffff;
+      int m = nxt;
+      for (int off = 16; off; off >>= 1) m = min(m, __shfl_xor_sync(mask, m, off));
+      cc = (m == 0x7fffffff) ? -1 : m;
+    }
+  }
+}
+
+void launch_residual(const double *U0, const double *UM, const ResidualTable *tab, int nv,
+                     long long NI, unsigned long long *out, cudaStream_t st) {
+  const long long n = (long long)nv * NI;
+  long long blocks = (n + 255) / 256;
+  if (blocks > 152LL * 16) blocks = 152LL * 16;
+  k_residual<<<(int)blocks, 256, 0, st>>>(U0, UM, tab, nv, NI, out);
+}
+
 __global__ void __launch_bounds__(256) k_exp(const Mech *__restrict__ m, const double *__restrict__ x,
                                              double *__restrict__ y, long long n) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;

@@ -116,6 +116,7 @@ inline __host__ __device__ int nQ(int ns) { return Q_NBASE + 6 * ns; }
 enum : unsigned { ST_NONCONV = 1u, ST_NONPHYS = 2u, ST_NONFINITE = 4u };
 
 // Host-side quadrature (Gauss-Lobatto nodes, Lagrange integration matrices).
+void narrow8_matrix(double m47, double m48, double M[8][8]);
 void lobatto_nodes(int n, std::vector<double> &x);
 void node_to_node_matrix(const std::vector<double> &nodes, std::vector<double> &S);
 void multirate_matrices(int coarse, int fine, int repeat, std::vector<double> &t1,
@@ -192,5 +193,16 @@ void launch_fine_chain(const DevState &s, const double *U0, double *U, const Fin
                        cudaStream_t st);
 void launch_chem_only(const DevState &s, const double *U, double *F2, cudaStream_t st);
 void launch_exp(const Mech *m, const double *x, double *y, long long n, cudaStream_t st);
+
+// Weights and sources of the collocation residual (device-resident table).
+constexpr int SMC_RES_MAX = 80;
+struct ResidualTable {
+  int n1, n2;
+  double c1[SMC_RES_MAX], c2[SMC_RES_MAX];
+  const double *src1[SMC_RES_MAX];
+  const double *src2[SMC_RES_MAX];
+};
+void launch_residual(const double *U0, const double *UM, const ResidualTable *tab, int nv,
+                     long long NI, unsigned long long *out, cudaStream_t st);
 
 }  // namespace smc

@@ -28,13 +28,13 @@ STATUS_NAMES = {0: "SMC_OK", 1: "SMC_ERR_ARG", 2: "SMC_ERR_CUDA", 3: "SMC_ERR_OO
 OPT = dict(precision=0, m47=1, m48=2, diffusion_mode=3, ref_species=4, xi_ratio=5,
            newton_tol=6, newton_maxit=7, t_guess=8, reactions=9, segment=10, profile=11,
            use_graphs=12, x_layout=13, march=14, rates=15,
-           fine_repeat=16)
+           fine_repeat=16, sdc_exit=17)
 KERNELS = ["prim", "grad", "march", "final", "update", "fine", "chem", "other"]
 
 EXPORTS = ["smc_create", "smc_destroy", "smc_rhs", "smc_sdc_step", "smc_prim_to_cons", "smc_autotune",
            "smc_set_stream", "smc_set_option", "smc_get_stats", "smc_synchronize",
            "smc_invalidate", "smc_collocation", "smc_multirate_collocation", "smc_rhs_noalloc",
-           "smc_exp", "smc_last_error"]
+           "smc_exp", "smc_heat2d", "smc_last_error"]
 
 
 class smc_grid(C.Structure):
@@ -60,7 +60,8 @@ class smc_stats(C.Structure):
     _fields_ = [("n_rhs", C.c_longlong), ("n_react", C.c_longlong), ("n_steps", C.c_longlong),
                 ("device_flags", C.c_uint), ("nvars", C.c_int), ("ncells", C.c_longlong),
                 ("device_bytes", C.c_longlong), ("launches", C.c_longlong * 8),
-                ("kernel_ms", C.c_double * 8)]
+                ("kernel_ms", C.c_double * 8), ("sweeps_done", C.c_int),
+                ("residual", C.c_double * 64)]
 
 
 def load_library(path: str = LIB_PATH) -> C.CDLL:
@@ -83,6 +84,8 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
     lib.smc_autotune.argtypes = [vp, vp, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]
     lib.smc_collocation.argtypes = [C.c_int, vp, vp]
     lib.smc_multirate_collocation.argtypes = [C.c_int, C.c_int, C.c_int, vp, vp, vp, vp]
+    lib.smc_heat2d.argtypes = [C.c_int, dp, vp, vp, vp, dp, dp, dp, dp, C.c_int, C.c_int, C.c_int,
+                               vp, C.POINTER(C.c_longlong), vp]
     lib.smc_exp.argtypes = [vp, vp, C.c_longlong]
     lib.smc_exp.restype = C.c_int
     lib.smc_rhs_noalloc.argtypes = [C.POINTER(C.c_int), C.POINTER(C.c_double),
@@ -146,6 +149,21 @@ def smc_multirate_collocation(coarse: int, fine: int, repeat: int = 1):
     if st != SMC_OK:
         raise SmcError(st, "smc_multirate_collocation")
     return t1, t2, S21, S22
+
+
+def smc_heat2d(N, h, a, b, G, u, t0, dt, nsteps, m47=3557.0 / 44100.0, m48=-2083.0 / 117600.0,
+               nodes=3, sweeps=4, stream=None):
+    """Advance the App. A heat problem in place (see smc.h); a, b, G (or
+    None), u: CUDA float64 tensors of N*N elements.  Returns the number of
+    operator evaluations."""
+    ev = C.c_longlong(0)
+    raw = getattr(stream, "cuda_stream", stream)
+    st = lib().smc_heat2d(int(N), float(h), _ptr(a), _ptr(b), _ptr(G) if G is not None else None,
+                          float(m47), float(m48), float(t0), float(dt), int(nsteps), int(nodes),
+                          int(sweeps), _ptr(u), C.byref(ev), C.c_void_p(raw))
+    if st != SMC_OK:
+        raise SmcError(st, "smc_heat2d")
+    return ev.value
 
 
 def smc_exp(x, y):
@@ -297,6 +315,7 @@ class Smc:
         out = {f: getattr(s, f) for f, _ in smc_stats._fields_}
         out["launches"] = dict(zip(KERNELS, list(s.launches)))
         out["kernel_ms"] = dict(zip(KERNELS, list(s.kernel_ms)))
+        out["residual"] = list(s.residual)[:max(s.sweeps_done, 0)]
         return out
 
     def close(self):

@@ -466,3 +466,27 @@ def workload(name: str, seed: int = 1, n: int | None = None) -> Workload:
         dt = 0.5 * _acoustic_dt(grid.dx[0], 2000.0, 2000.0)
         return Workload(name, grid, mech, global_to_boxes(grid, g), dt, 5, 8, 5, 50, "mixed")
     raise ValueError(f"unknown workload {name!r}")
+
+
+# ------------------------------------------------------------------ App. A
+def heat_fields(problem: str, N: int) -> dict:
+    """Inputs of the appendix heat problems on the periodic square
+    [0, 2 pi]^2 with x_i = 2 pi i / N (row-major [y][x]):
+      T1: a = b = 1 + 0.1 cos x cos y, source exp(-t) G with
+          G = (1 + 0.4 cos x cos y) sin x sin y (exact u = exp(-t) sin x sin y);
+      T2: a = 1 + 0.9 cos 2x sin(2y + pi/3), b = 1 + 0.9 cos(2x + pi/3) sin 2y,
+          no source.
+    u0 = sin x sin y for both.  Returns dict(h, a, b, G (or None), u0)."""
+    x = 2.0 * np.pi * np.arange(N) / N
+    Y, X = np.meshgrid(x, x, indexing="ij")
+    h = 2.0 * np.pi / N
+    ss = np.sin(X) * np.sin(Y)
+    if problem == "T1":
+        cc = np.cos(X) * np.cos(Y)
+        a = 1.0 + 0.1 * cc
+        return dict(h=h, a=a, b=a.copy(), G=(1.0 + 0.4 * cc) * ss, u0=ss.copy())
+    if problem == "T2":
+        a = 1.0 + 0.9 * np.cos(2 * X) * np.sin(2 * Y + np.pi / 3)
+        b = 1.0 + 0.9 * np.cos(2 * X + np.pi / 3) * np.sin(2 * Y)
+        return dict(h=h, a=a, b=b, G=None, u0=ss.copy())
+    raise ValueError(problem)

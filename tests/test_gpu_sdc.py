@@ -202,3 +202,55 @@ def test_eval_counts_reproduce_table_mrsdc_runtime(smc):
             assert (st["n_rhs"], st["n_react"]) == (n_ad, n_r)
         checked += 1
     assert checked == 4
+
+
+def test_sdc_residual_early_exit_matches_oracle(smc):
+    """eq. residual with the early exit (eps = 0.5, up to 14 sweeps): the
+    library's residual after every sweep equals the oracle's while it is far
+    above rounding, both stop within one sweep of each other once it
+    stagnates, and the state agrees."""
+    wl, U, U_g = state("c1", seed=2, p_amp=0.03)
+    with smc.Smc(wl.grid, wl.mech, {"sdc_exit": 0.5}) as h:
+        Ud = dev(U)
+        h.sdc_step(Ud, wl.dt, nodes=3, sweeps=14)
+        h.synchronize()
+        st = h.stats()
+        U1 = Ud.cpu().numpy()
+    ref, _, nev, hist = osdc.sdc_step_exit(U_g, oracle_f(wl), wl.dt, nodes=3, max_sweeps=14,
+                                           eps=0.5)
+    got = st["residual"]
+    assert len(got) == st["sweeps_done"] < 14
+    assert abs(st["sweeps_done"] - len(hist)) <= 1
+    assert st["n_rhs"] == 1 + 2 * st["sweeps_done"]
+    for g, o in zip(got, hist):
+        if o > 1e-11:
+            assert abs(g - o) <= 1e-3 * o, (got, hist)
+    ref = synth.global_to_boxes(wl.grid, ref)
+    assert relerr(U1 - U, ref - U).max() < TOL
+
+
+def test_mrsdc_residual_early_exit_matches_oracle(smc):
+    """The multirate residual (coarse quadrature of f1, fine quadrature of
+    f2) with the early exit, 8 boxes, 21 species."""
+    wl = synth.workload("c4", seed=2, n=10)
+    from oracle import thermo
+    prim_g = synth.boxes_to_global(wl.grid, wl.prim)
+    U_g = thermo.conserved(prim_g, wl.mech.nasa7, wl.mech.W)
+    U = synth.global_to_boxes(wl.grid, U_g)
+    with smc.Smc(wl.grid, wl.mech, {"sdc_exit": 0.5}) as h:
+        Ud = dev(U)
+        h.sdc_step(Ud, wl.dt, nodes=3, sweeps=14, reaction_substeps=5)
+        h.synchronize()
+        st = h.stats()
+        U1 = Ud.cpu().numpy()
+    hist = []
+    ref, _, _, n1, n2 = osdc.mrsdc_step(U_g, oracle_f(wl, "transport"), oracle_f(wl, "chem"),
+                                        wl.dt, coarse=3, fine=5, sweeps=14, eps=0.5,
+                                        history=hist)
+    got = st["residual"]
+    assert abs(st["sweeps_done"] - len(hist)) <= 1 and st["sweeps_done"] < 14
+    for g, o in zip(got, hist):
+        if o > 1e-11:
+            assert abs(g - o) <= 1e-3 * o, (got, hist)
+    ref = synth.global_to_boxes(wl.grid, ref)
+    assert relerr(U1 - U, ref - U).max() < TOL

@@ -173,3 +173,54 @@ def test_heat_T1_80_and_rate():
     assert abs(linf / g[("SMC", 80)][0] - 1) < 0.05
     rate = math.log2(g[("SMC", 40)][0] / linf)
     assert 7.8 < rate < 8.2
+
+
+def _collocation_linear(lam, dt, nodes):
+    """Closed form of the Gauss-Lobatto collocation solution of u' = lam u,
+    u(0) = 1, over one step: U = 1 + dt lam Q U at every node."""
+    tau = sdc.gauss_lobatto(nodes)
+    Q = np.vstack([np.zeros(nodes), sdc.q_matrix(tau)])      # row 0: U_0 itself
+    return np.linalg.solve(np.eye(nodes) - dt * lam * Q, np.ones(nodes))
+
+
+@pytest.mark.parametrize("nodes", [3, 5])
+def test_residual_vanishes_at_the_collocation_solution(nodes):
+    """eq. residual: the residual is zero at the collocation solution (in
+    closed form for u' = lam u), the SDC sweeps drive it there, and the early
+    exit stops once it stagnates, with U_M at the collocation value."""
+    lam, dt = -3.0, 0.05
+    Uc = _collocation_linear(lam, dt, nodes)
+    tau = sdc.gauss_lobatto(nodes)
+    F = [np.array([lam * u]) for u in Uc]
+    R = sdc.sdc_residual(np.array([1.0]), np.array([Uc[-1]]), F, dt, nodes)
+    assert abs(R[0]) < 1e-15
+    U, _, nev, hist = sdc.sdc_step_exit(np.array([1.0]), lambda u, t: lam * u, dt, nodes=nodes,
+                                        max_sweeps=40, eps=0.5)
+    assert abs(U[0] - Uc[-1]) < 1e-15
+    # geometric decrease, then the stop once the ratio falls below 1.5
+    assert all(hist[i] > 2 * hist[i + 1] for i in range(len(hist) - 2) if hist[i + 1] > 1e-14)
+    assert len(hist) < 40 and hist[-1] < 1e-14
+    assert nev == 1 + len(hist) * (nodes - 1)
+
+
+def test_residual_norm_is_per_component_relative():
+    R = np.array([[1e-3, -2e-3], [5.0, 0.0]])
+    U0 = np.array([[1.0, -4.0], [1e4, 2e4]])
+    assert sdc.residual_norm(R, U0) == pytest.approx(max(2e-3 / 4.0, 5.0 / 2e4))
+    assert sdc.stop_rule([1e-3, 9e-4], 0.5) and not sdc.stop_rule([1e-3, 1e-5], 0.5)
+    assert sdc.stop_rule([1e-3, 0.0], 0.5)
+
+
+def test_mrsdc_residual_exit_reaches_the_multirate_collocation_solution():
+    """The multirate residual (coarse quadrature of f1 plus fine quadrature
+    of f2) is driven to rounding level by repeated sweeps and the exit stops
+    there; the state then agrees with a 60-sweep run."""
+    f1 = lambda u: -1.0 * u
+    f2 = lambda u: -4.0 * u
+    hist = []
+    U, _, _, _, _ = sdc.mrsdc_step(np.array([1.0]), f1, f2, 0.05, coarse=3, fine=5, repeat=1,
+                                   sweeps=60, eps=0.5, history=hist)
+    Uref, _, _, _, _ = sdc.mrsdc_step(np.array([1.0]), f1, f2, 0.05, coarse=3, fine=5,
+                                      sweeps=60)
+    assert len(hist) < 60 and hist[-1] < 1e-14
+    assert abs(U[0] - Uref[0]) < 1e-15
