@@ -33,6 +33,11 @@ Discretisation (readings of the paper, collected in the design doc):
   for k != ref, F_ref = -sum_{k != ref} F_k, and the energy flux uses
   h_k - h_ref.
 * Chemistry: rho omega_k from ``chem.production_rates``.
+* Non-periodic x ends (Options.x_outflow): every x derivative -- convective,
+  narrow, mixed, velocity gradients, correction velocity -- uses the
+  boundary-lowered stencils of ``stencil.D_bc`` / ``stencil.narrow_bc`` in
+  the four cells next to each end (Sec. 2.2, boundary paragraph); no
+  characteristic boundary correction.
 """
 from __future__ import annotations
 
@@ -55,6 +60,7 @@ class Options:
     ref: int = -1                   # reference species index (mode "ref")
     T0: float = 1000.0              # Newton first guess
     reactions: bool = True
+    x_outflow: bool = False         # x ends are non-periodic boundaries (lowered stencils)
 
 
 def _inner(f, dirs):
@@ -105,16 +111,22 @@ def rhs_ghosted(Ug: np.ndarray, mech, dx, opt: Options | None = None,
         def lin(a):                         # ghosted along d only
             return _inner(a, [e, f])
 
+        bc = opt.x_outflow and d == 0
+
         def Dd(a):                          # D_d of a field ghosted along d
-            return stencil.D(a, ax, hd)
+            return stencil.D_bc(a, ax, hd) if bc else stencil.D(a, ax, hd)
 
         def nd(a, u):                       # narrow along d
+            if bc:
+                return stencil.narrow_bc(lin(a), lin(u), ax, hd, M)
             return stencil.narrow(lin(a), lin(u), ax, hd, M)
 
         def grad(comp, along):
             """D_along of vel[comp] on cells interior except along d."""
             third = [k for k in range(3) if k not in (along, d)]
             arr = _inner(vel[comp], third)
+            if opt.x_outflow and along == 0:
+                return stencil.D_bc(arr, AX[along], dx[along])
             return stencil.D(arr, AX[along], dx[along])
 
         ud = vel[d]
@@ -185,7 +197,9 @@ def pad_periodic(U: np.ndarray) -> np.ndarray:
 
 
 def rhs_periodic(U: np.ndarray, mech, dx, opt: Options | None = None, parts=False):
-    """Right-hand side on a triply periodic domain, U: [NV, nz, ny, nx]."""
+    """Right-hand side on a triply periodic domain, U: [NV, nz, ny, nx].
+    With ``opt.x_outflow`` the x ends are boundaries instead: the lowered
+    stencils never read the wrapped x ghosts."""
     return rhs_ghosted(pad_periodic(U), mech, dx, opt, parts)
 
 

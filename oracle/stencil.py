@@ -148,3 +148,100 @@ def wide(a: np.ndarray, u: np.ndarray, axis: int, h: float) -> np.ndarray:
     """The wide alternative D(a D u) (Sec. 1), needs 8 ghosts; comparison only."""
     du = D(u, axis, h, g=4)          # 4 ghosts left
     return D(_take(a, axis, 4, du.shape[axis]) * du, axis, h, g=4)
+
+
+# ------------------------------------------------------------ boundaries
+# Near a non-periodic boundary (Sec. 2.2, boundary paragraph) the stencils
+# are lowered: the fourth cell from the boundary (index 3 counted from it)
+# uses 6th-order centred stencils, the third (index 2) 4th-order centred
+# ones, the second (index 1) the centred 2nd-order diffusion and a biased
+# 3rd-order advection stencil, and the boundary cell (index 0) completely
+# biased stencils: 2nd order for diffusion, 3rd order for advection.  Only
+# cells inside the domain are read.
+
+D6 = (Fr(3, 4), Fr(-3, 20), Fr(1, 60))
+D4 = (Fr(2, 3), Fr(-1, 12))
+# one-sided first derivatives from the four cells nearest the boundary,
+# exact on cubics: at the cell next to it (biased) and at it (completely biased)
+DB1 = (Fr(-2, 6), Fr(-3, 6), Fr(6, 6), Fr(-1, 6))
+DB0 = (Fr(-11, 6), Fr(18, 6), Fr(-9, 6), Fr(2, 6))
+
+# Free parameters of the 4th-order narrow stencil.  Polynomial exactness
+# (deg a + deg u <= 5), zero row sums and the antisymmetry of the 8th- and
+# 6th-order matrices leave two parameters p = M[3][1], q = M[3][2].  The
+# paper's rule (minimise the sum of the absolute leading truncation
+# coefficients) reproduces its own 6th- and 8th-order choices but leaves a
+# triangle of optima here; minimising the next-order coefficients on it
+# leaves an edge (q = 1/72), whose midpoint p = -1/9 is taken.
+M4_P, M4_Q = Fr(-1, 9), Fr(1, 72)
+
+
+def narrow4_exact(p=M4_P, q=M4_Q):
+    """The 4x4 M of the 4th-order narrow stencil (s = 2), rows and columns
+    -1..2, in terms of its two free parameters."""
+    p, q = Fr(p), Fr(q)
+    return [[-q, -p, 2 * p + 3 * q + Fr(1, 12), -p - 2 * q - Fr(1, 12)],
+            [p + 4 * q + Fr(1, 6), -3 * q - Fr(3, 4), -3 * p - 6 * q + Fr(5, 12), 2 * p + 5 * q + Fr(1, 6)],
+            [-2 * p - 5 * q - Fr(1, 6), 3 * p + 6 * q - Fr(5, 12), 3 * q + Fr(3, 4), -p - 4 * q - Fr(1, 6)],
+            [p + 2 * q + Fr(1, 12), -2 * p - 3 * q - Fr(1, 12), p, q]]
+
+
+def narrow2_exact():
+    """The centred 2nd-order flux H_{i+1/2} = (a_i + a_{i+1})/2 (u_{i+1} - u_i)
+    as a 2x2 M."""
+    return [[Fr(-1, 2), Fr(1, 2)], [Fr(-1, 2), Fr(1, 2)]]
+
+
+def _last(f, axis):
+    return np.moveaxis(f, axis, -1)
+
+
+def D_bc(f: np.ndarray, axis: int, h: float, g: int = 4) -> np.ndarray:
+    """First derivative along ``axis`` whose two ends are non-periodic
+    boundaries: D8 in the interior, lowered at the four cells next to each
+    end.  ``f`` carries g ghosts along the axis, which are never read by
+    the lowered cells (the interior cells never reach them either)."""
+    out = D(f, axis, h, g)
+    n = out.shape[axis]
+    t = f.dtype.type
+    c = lambda r: t(r.numerator) / t(r.denominator)
+    fi = _last(_take(f, axis, g, n), axis)        # the domain's cells, axis last
+    o = _last(out, axis)                          # a view: writes go to out
+    for side in (0, 1):
+        v = fi if side == 0 else fi[..., ::-1]    # mirrored for the high end
+        sgn = 1.0 if side == 0 else -1.0
+        k = (lambda j: j) if side == 0 else (lambda j: n - 1 - j)
+        o[..., k(0)] = sgn * sum(c(w) * v[..., j] for j, w in enumerate(DB0)) / h
+        o[..., k(1)] = sgn * sum(c(w) * v[..., j] for j, w in enumerate(DB1)) / h
+        o[..., k(2)] = sgn * sum(c(w) * (v[..., 2 + j + 1] - v[..., 2 - j - 1]) for j, w in enumerate(D4)) / h
+        o[..., k(3)] = sgn * sum(c(w) * (v[..., 3 + j + 1] - v[..., 3 - j - 1]) for j, w in enumerate(D6)) / h
+    return out
+
+
+def narrow_bc(a: np.ndarray, u: np.ndarray, axis: int, h: float, M8: np.ndarray,
+              g: int = 4) -> np.ndarray:
+    """(a u_x)_x along ``axis`` with non-periodic ends: the 8th-order narrow
+    stencil in the interior, the 6th-, 4th- and 2nd-order narrow stencils at
+    the fourth, third and second cells from each end, and at the end cell
+    a u_xx + a_x u_x from one-sided 2nd-order differences,
+      u_xx ~ (2 u0 - 5 u1 + 4 u2 - u3)/h^2,  u_x ~ (-3 u0 + 4 u1 - u2)/(2h),
+    the same for a_x (mirrored at the high end)."""
+    out = narrow(a, u, axis, h, M8, g)
+    n = out.shape[axis]
+    dt = np.result_type(a, u, M8)
+    ai = _take(a, axis, g, n)
+    ui = _take(u, axis, g, n)
+    o = _last(out, axis)
+    for s, M in ((3, narrow6_exact()), (2, narrow4_exact()), (1, narrow2_exact())):
+        r = _last(narrow(ai, ui, axis, h, to_float(M, dt), g=s), axis)   # cells s .. n-1-s
+        o[..., s] = r[..., 0]
+        o[..., n - 1 - s] = r[..., -1]
+    al, ul = _last(ai, axis), _last(ui, axis)
+    for side in (0, 1):
+        av = al if side == 0 else al[..., ::-1]
+        uv = ul if side == 0 else ul[..., ::-1]
+        uxx = 2 * uv[..., 0] - 5 * uv[..., 1] + 4 * uv[..., 2] - uv[..., 3]
+        ux = -3 * uv[..., 0] + 4 * uv[..., 1] - uv[..., 2]
+        ax_ = -3 * av[..., 0] + 4 * av[..., 1] - av[..., 2]
+        o[..., 0 if side == 0 else n - 1] = (av[..., 0] * uxx + 0.25 * ax_ * ux) / (h * h)
+    return out

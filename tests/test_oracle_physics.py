@@ -177,3 +177,22 @@ def test_rhs_spatial_order_eight():
     e2 = np.abs(vals[64][:, 0] - vals[128][:, 0, ::2, ::2]).max(axis=(1, 2))
     rates = np.log2(e1 / e2)
     assert (rates > 7.5).all() and (rates < 8.5).all(), rates
+
+
+def test_x_outflow_rhs_changes_only_the_cells_near_the_x_ends():
+    """With non-periodic x ends the right-hand side equals the periodic one
+    at every cell four or more cells from both x ends (same stencils, same
+    data), differs next to the ends, and still vanishes (transport) on a
+    uniform state."""
+    from util import state
+    wl, U, U_g = state("c1", seed=4, p_amp=0.03)
+    opt = rhs.Options(x_outflow=True)
+    per = rhs.rhs_periodic(U_g, wl.mech, wl.grid.dx)
+    out = rhs.rhs_periodic(U_g, wl.mech, wl.grid.dx, opt)
+    nx = U_g.shape[-1]
+    assert np.array_equal(per[..., 4:nx - 4], out[..., 4:nx - 4])
+    for c in (0, 3, nx - 4, nx - 1):
+        assert np.abs(per[..., c] - out[..., c]).max() > 0
+    uni = np.broadcast_to(U_g[:, :1, :1, :1], U_g.shape).copy()
+    tr, _ = rhs.rhs_periodic(uni, wl.mech, wl.grid.dx, opt, parts=True)
+    assert np.abs(tr).max() <= 1e-9 * np.abs(uni).max()
