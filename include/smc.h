@@ -100,8 +100,14 @@ typedef struct {
 } smc_mechanism;
 
 enum { SMC_BC_PERIODIC = 0, SMC_BC_OUTFLOW = 1 };
-/* Boundary kind of each domain face.  This version supports periodic faces
- * only; any other value returns SMC_ERR_ARG. */
+/* Boundary kind of each domain face.  y and z must be periodic.  x is
+ * periodic, or SMC_BC_OUTFLOW on both ends: every x derivative in the four
+ * cells next to an end then uses the boundary-lowered stencils of Sec. 2.2
+ * (6th-, 4th- and 2nd-order centred diffusion and first derivatives at the
+ * fourth, third and second cells, completely biased ones at the end cell),
+ * without a characteristic boundary correction.  Outflow x needs at least
+ * 8 cells along x and boxes at least 3 cells wide.  Other combinations
+ * return SMC_ERR_ARG.  A NULL bc means periodic everywhere. */
 typedef struct { int lo[3], hi[3]; } smc_bc;
 
 /* Options for smc_set_option (value given as a double). */

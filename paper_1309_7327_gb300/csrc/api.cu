@@ -29,6 +29,10 @@ struct smc_handle {
   int rates32 = 0;                      // FP32-mantissa production rates (mixed only)
   int fine_repeat = 1;                  // groups of fine nodes per coarse interval (type (c) if > 1)
   double sdc_exit = 0.0;                // residual early exit threshold (0: off)
+  int x_outflow = 0;                    // non-periodic x ends
+  int nx_domain = 0;
+  std::vector<BcCell> hbc;              // cells next to the x ends
+  BcCell *d_bc = nullptr;
   int sweeps_done = 0;
   double resid[64] = {};
   ResidualTable *d_restab = nullptr;
@@ -182,6 +186,10 @@ DevState state(smc_handle *h) {
   s.opt = h->opt;
   s.opt.rates32 = h->rates32 && h->precision == 1;
   s.xi_ratio_f = (float)h->opt.xi_ratio;
+  s.x_outflow = h->x_outflow;
+  s.nx_domain = h->nx_domain;
+  s.bc_cells = h->d_bc;
+  s.n_bc = (long long)h->hbc.size();
   return s;
 }
 
@@ -350,10 +358,17 @@ smc_status eval_rhs(smc_handle *h, const double *U, double *F, int transport, in
       sx.lines[0] = h->d_lines_xt;
     }
     for (int d = 0; d < 3; ++d) {
-      Timed t(h, SMC_K_MARCH);
-      if (mixed && h->march[1]) launch_march_m2(d == 0 ? sx : s, d, h->d_dUf, d == 0, h->stream);
-      else if (mixed) launch_march_m(d == 0 ? sx : s, d, h->d_dUf, d == 0, h->stream);
-      else launch_march(d == 0 ? sx : s, d, F, d == 0, h->stream);
+      {
+        Timed t(h, SMC_K_MARCH);
+        if (mixed && h->march[1]) launch_march_m2(d == 0 ? sx : s, d, h->d_dUf, d == 0, h->stream);
+        else if (mixed) launch_march_m(d == 0 ? sx : s, d, h->d_dUf, d == 0, h->stream);
+        else launch_march(d == 0 ? sx : s, d, F, d == 0, h->stream);
+      }
+      if (d == 0 && h->x_outflow && !h->hbc.empty()) {
+        // the cells next to the x ends: lowered stencils replace the x terms
+        Timed t(h, SMC_K_MARCH);
+        if (mixed) launch_xbc_m(s, h->d_dUf, h->stream); else launch_xbc(s, F, h->stream);
+      }
     }
   }
   if (mixed) {
@@ -495,36 +510,32 @@ smc_status sdc_multirate(smc_handle *h, double *U, const void *key, double dt, i
   if (M1 > 4 || sub > 8 || M2 > 64) return fail(h, SMC_ERR_ARG, "too many multirate nodes");
   std::vector<double> t1, t2, S21, S22;
   multirate_matrices(coarse, fine, repeat, t1, t2, S21, S22);
-  smc_status st = ensure_pools(h, 2 * M1 + 1, 2 * M2 + 1);
+  // transport terms: two sets of coarse-node arrays (old / new sweep) and the
+  // shared f1(U_0) in slot 0.  Reaction terms: one array per fine node, slot
+  // t for node t (the recycled f2(U_0) in slot 0), updated in place group by
+  // group, plus `fine` scratch arrays (slots M2 + 1 ..) that take a group's
+  // new values while its own chain still reads the old ones.
+  smc_status st = ensure_pools(h, 2 * M1 + 1, M2 + 1 + fine);
   if (st) return st;
   const long long n = (long long)h->nv * h->ncells;
+  const size_t rbytes = (size_t)h->ns * h->ncells * sizeof(double);
   CUDA_TRY(h, cudaMemcpyAsync(h->d_U0, U, n * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
-  int f0, r0;
-  if (h->cache_kind == 2 && h->cache_U == key && h->cache_f >= 0 && h->cache_r >= 0) {
-    f0 = h->cache_f;
-    r0 = h->cache_r;
-  } else {
-    f0 = 0;
-    r0 = 0;
+  const int f0 = 0, r0 = 0;
+  if (!(h->cache_kind == 2 && h->cache_U == key && h->cache_f == 0 && h->cache_r == 0)) {
     st = eval_rhs(h, h->d_U0, h->fpool[f0], 1, 0);
     if (st) return st;
     { Timed t(h, SMC_K_CHEM); launch_chem_only(state(h), h->d_U0, h->rpool[r0], h->stream); }
     h->n_rhs++;
     h->n_react++;
   }
-  std::vector<int> fo, ro;
-  for (int i = 0; i < 2 * M1 + 1; ++i)
-    if (i != f0) fo.push_back(i);
-  for (int i = 0; i < 2 * M2 + 1; ++i)
-    if (i != r0) ro.push_back(i);
-  std::vector<int> f1old(M1 + 1, f0), f1new(M1 + 1, f0), f2old(M2 + 1, r0), f2new(M2 + 1, r0);
+  std::vector<int> fo;
+  for (int i = 1; i < 2 * M1 + 1; ++i) fo.push_back(i);
+  std::vector<int> f1old(M1 + 1, f0), f1new(M1 + 1, f0);
   int set = 0;
   DevState s = state(h);
   for (int k = 0; k < sweeps; ++k) {
     f1new[0] = f0;
-    f2new[0] = r0;
     for (int p = 1; p <= M1; ++p) f1new[p] = fo[set * M1 + p - 1];
-    for (int q = 1; q <= M2; ++q) f2new[q] = ro[set * M2 + q - 1];
     for (int p = 0; p < M1; ++p) {
       if (p > 0) {
         st = eval_rhs(h, U, h->fpool[f1new[p]], 1, 0);
@@ -553,22 +564,30 @@ smc_status sdc_multirate(smc_handle *h, double *U, const void *key, double dt, i
         }
         fc.F1new_p = h->fpool[f1new[p]];
         for (int j = 0; j <= M1; ++j) fc.F1old[j] = h->fpool[f1old[j]];
+        // old values: f2(U_0) everywhere in the first sweep (spread start),
+        // then the node's slot, which no earlier group of this sweep has
+        // overwritten (a group writes its own nodes, its end node excepted)
         for (int t = 0; t <= sub; ++t) {
-          fc.F2old[t] = h->rpool[f2old[fc.q0 + t]];
-          fc.F2new[t] = h->rpool[f2new[fc.q0 + t]];
+          fc.F2old[t] = h->rpool[k == 0 ? r0 : fc.q0 + t];
+          fc.F2new[t] = h->rpool[M2 + 1 + t];
         }
         fc.eval_first = fc.q0 > 0;
         fc.eval_last = (p == M1 - 1 && r == repeat - 1);
         const bool first = p == 0 && r == 0;
         { Timed t(h, SMC_K_FINE); launch_fine_chain(s, first ? h->d_U0 : U, U, fc, h->stream); }
         h->n_react += sub - (fc.eval_first ? 0 : 1) + (fc.eval_last ? 1 : 0);
+        // the group's new values into their node slots
+        for (int t = fc.eval_first ? 0 : 1; t <= sub; ++t) {
+          if (t == sub && !fc.eval_last) break;
+          CUDA_TRY(h, cudaMemcpyAsync(h->rpool[fc.q0 + t], h->rpool[M2 + 1 + t], rbytes,
+                                      cudaMemcpyDeviceToDevice, h->stream));
+        }
       }
     }
     st = eval_rhs(h, U, h->fpool[f1new[M1]], 1, 0);
     if (st) return st;
     h->n_rhs++;
     f1old = f1new;
-    f2old = f2new;
     set ^= 1;
     h->sweeps_done = k + 1;
     if (h->sdc_exit > 0.0) {
@@ -588,20 +607,20 @@ smc_status sdc_multirate(smc_handle *h, double *U, const void *key, double dt, i
         double q = 0.0;
         for (int qq = 0; qq < M2; ++qq) q += S22[qq * (M2 + 1) + t];
         tab.c2[t] = dt * q;
-        tab.src2[t] = h->rpool[f2new[t]];
+        tab.src2[t] = h->rpool[t];
       }
       double r;
       if ((st = sweep_residual(h, h->d_U0, U, tab, r))) return st;
       if (residual_says_stop(h, k, r)) break;
     }
   }
+  // keep f1(U_M) and f2(U_M) in slot 0 so that every recycled step issues the
+  // same launches on the same buffers (the step can then be replayed as a graph)
   if (f1old[M1] != 0)
     CUDA_TRY(h, cudaMemcpyAsync(h->fpool[0], h->fpool[f1old[M1]], n * sizeof(double),
                                 cudaMemcpyDeviceToDevice, h->stream));
-  if (f2old[M2] != 0)
-    CUDA_TRY(h, cudaMemcpyAsync(h->rpool[0], h->rpool[f2old[M2]],
-                                (size_t)h->ns * h->ncells * sizeof(double), cudaMemcpyDeviceToDevice,
-                                h->stream));
+  CUDA_TRY(h, cudaMemcpyAsync(h->rpool[0], h->rpool[M2], rbytes, cudaMemcpyDeviceToDevice,
+                              h->stream));
   CUDA_TRY(h, cudaGetLastError());
   h->cache_kind = 2;
   h->cache_U = (const double *)key;
@@ -626,9 +645,12 @@ smc_status smc_create(const smc_grid *grid, const smc_mechanism *mech, const smc
     return st;
   };
   if (bc) {
-    for (int d = 0; d < 3; ++d)
+    for (int d = 1; d < 3; ++d)
       if (bc->lo[d] != SMC_BC_PERIODIC || bc->hi[d] != SMC_BC_PERIODIC)
-        return bail(fail(h, SMC_ERR_ARG, "only periodic boundaries are supported"));
+        return bail(fail(h, SMC_ERR_ARG, "y and z boundaries must be periodic"));
+    if (bc->lo[0] != bc->hi[0] || (bc->lo[0] != SMC_BC_PERIODIC && bc->lo[0] != SMC_BC_OUTFLOW))
+      return bail(fail(h, SMC_ERR_ARG, "x boundaries must be both periodic or both outflow"));
+    h->x_outflow = bc->lo[0] == SMC_BC_OUTFLOW;
   }
   // ---- mechanism
   if (const char *why = pack_mechanism(mech, 1024, h->hmech, h->hrx))
@@ -666,6 +688,8 @@ smc_status smc_create(const smc_grid *grid, const smc_mechanism *mech, const smc
     B.gz = n[2] + 2 * SMC_GHOST;
     B.off_g = offg;
     B.off_i = offi;
+    for (int d = 0; d < 3; ++d) B.lo[d] = grid->lo[3 * b + d];
+    B.pad = 0;
     offg += (long long)B.gx * B.gy * B.gz;
     offi += (long long)B.nx * B.ny * B.nz;
     for (int k = 0; k < n[2]; ++k)
@@ -679,6 +703,29 @@ smc_status smc_create(const smc_grid *grid, const smc_mechanism *mech, const smc
   }
   h->ncells = offi;
   h->nghost = offg;
+  h->nx_domain = grid->domain[0];
+  if (h->x_outflow && grid->domain[0] < 8)
+    return bail(fail(h, SMC_ERR_ARG, "outflow x ends need at least 8 cells along x"));
+  if (h->x_outflow) {
+    // the cells within four of either x end
+    for (int b = 0; b < h->nboxes; ++b) {
+      const Box &B = h->boxes[b];
+      if (B.nx < 3) return bail(fail(h, SMC_ERR_ARG, "boxes need at least 3 cells along x"));
+      for (int k = 0; k < B.nz; ++k)
+        for (int j = 0; j < B.ny; ++j)
+          for (int i = 0; i < B.nx; ++i) {
+            const int gxi = B.lo[0] + i;
+            const int dl = gxi, dh = grid->domain[0] - 1 - gxi;
+            if (dl > 3 && dh > 3) continue;
+            BcCell c;
+            c.g = B.off_g + ((long long)(k + SMC_GHOST) * B.gy + (j + SMC_GHOST)) * B.gx + (i + SMC_GHOST);
+            c.i = B.off_i + ((long long)k * B.ny + j) * B.nx + i;
+            c.side = dl <= 3 ? 0 : 1;
+            c.k = dl <= 3 ? dl : dh;
+            h->hbc.push_back(c);
+          }
+    }
+  }
   if (h->nghost >= (1LL << 31) || h->ncells * (long long)h->nv >= (1LL << 62))
     return bail(fail(h, SMC_ERR_ARG, "grid too large"));
   std::vector<int> gmap((size_t)h->nghost);
@@ -735,6 +782,10 @@ smc_status smc_create(const smc_grid *grid, const smc_mechanism *mech, const smc
   TRY_ALLOC(cudaMemcpy(h->d_gmap, gmap.data(), gmap.size() * sizeof(int), cudaMemcpyHostToDevice));
   TRY_ALLOC(dalloc(h, &h->d_imap, (size_t)h->ncells));
   TRY_ALLOC(cudaMemcpy(h->d_imap, imap.data(), imap.size() * sizeof(long long), cudaMemcpyHostToDevice));
+  if (!h->hbc.empty()) {
+    TRY_ALLOC(dalloc(h, &h->d_bc, h->hbc.size()));
+    TRY_ALLOC(cudaMemcpy(h->d_bc, h->hbc.data(), h->hbc.size() * sizeof(BcCell), cudaMemcpyHostToDevice));
+  }
   TRY_ALLOC(dalloc(h, &h->d_Q, (size_t)nQ(ns) * h->nghost));
   TRY_ALLOC(dalloc(h, &h->d_G, (size_t)9 * h->nghost));
   TRY_ALLOC(cudaMemset(h->d_G, 0, (size_t)9 * h->nghost * sizeof(double)));
@@ -779,6 +830,7 @@ smc_status smc_destroy(smc_handle *h) {
   cudaFree(h->d_U0);
   cudaFree(h->d_dUf);
   cudaFree(h->d_restab);
+  cudaFree(h->d_bc);
   cudaFree(h->d_resout);
   for (int i = 0; i < 3; ++i) cudaFree(h->d_stage[i]);
   drop_graph(h);

@@ -10,23 +10,12 @@
 // lambda, rho D_k, B_k, ...) are plain floats.  Products that form
 // convective fluxes (rho u_d, rho u_c u_d, rho H u_d, rho Y_k u_d) are
 // carried as float pairs through an FMA-based exact product.
+#include "bc.cuh"
 #include "chem.cuh"
 #include "smc_internal.h"
 
 namespace smc {
 
-// float-plane indices of the mixed-precision scratch (reuses the FP64 Q buffer)
-enum {
-  PM_U = 0, PM_V = 2, PM_W = 4, PM_T = 6, PM_P = 8, PM_KX = 10, PM_KY = 12, PM_KZ = 14,
-  PM_HMIX = 16, PM_RHO = 18, PM_RHOH = 20,
-  PM_C43 = 22, PM_ETA, PM_C23, PM_LAM, PM_AP, PM_SB, PM_NBASE
-};
-__host__ __device__ inline int pmY(int ns, int k) { return PM_NBASE + 2 * k; }
-__host__ __device__ inline int pmX(int ns, int k) { return PM_NBASE + 2 * ns + 2 * k; }
-__host__ __device__ inline int pmRY(int ns, int k) { return PM_NBASE + 4 * ns + 2 * k; }
-__host__ __device__ inline int pmRD(int ns, int k) { return PM_NBASE + 6 * ns + k; }
-__host__ __device__ inline int pmRDH(int ns, int k) { return PM_NBASE + 7 * ns + k; }
-__host__ __device__ inline int pmB(int ns, int k) { return PM_NBASE + 8 * ns + k; }
 int nQm(int ns) { return PM_NBASE + 9 * ns; }
 
 struct f2 {
@@ -156,6 +145,7 @@ __global__ void __launch_bounds__(128) k_prim_m(const DevState s, const double *
 // ------------------------------------------------------------ k_grad_m
 struct GradParamsM {
   float D[3][4];
+  double ihx;                     // 1/h_x (boundary-lowered x derivatives, FP64)
 };
 
 __device__ __forceinline__ int find_box_m(const Box *__restrict__ b, int nb, long long g) {
@@ -181,14 +171,29 @@ __global__ void __launch_bounds__(128) k_grad_m(const DevState s, const GradPara
     const long long stride[3] = {1, B.gx, (long long)B.gx * B.gy};
     int ng = 0;
     for (int e = 0; e < 3; ++e) ng += (crd[e] < 0 || crd[e] >= n[e]);
+    // cells next to non-periodic x ends take the lowered x derivative (FP64)
+    const int gxi = B.lo[0] + crd[0];
+    const int kb = !s.x_outflow ? -1
+                   : (gxi >= 0 && gxi < 4) ? gxi
+                   : (gxi >= s.nx_domain - 4 && gxi < s.nx_domain) ? s.nx_domain - 1 - gxi : -1;
     for (int e = 0; e < 3; ++e) {
       if (crd[e] < 0 || crd[e] >= n[e] || ng > 1) continue;
       for (int c = 0; c < 3; ++c) {
         float acc = 0.0f;
+        if (e == 0 && kb >= 0) {
+          const long long sg = gxi < 4 ? 1 : -1;
+          double v[7];
+          for (int j = 0; j < 7; ++j) {
+            const f2 pr = get_pair(Qf, NG, PM_U + 2 * c, g + sg * (j - kb));
+            v[j] = (double)pr.h + (double)pr.l;
+          }
+          acc = (float)((double)sg * lowered_d(v, kb) * P.ihx);
+        } else {
 #pragma unroll
-        for (int k = 1; k <= 4; ++k)
-          acc += P.D[e][k - 1] * diff(get_pair(Qf, NG, PM_U + 2 * c, g + k * stride[e]),
-                                      get_pair(Qf, NG, PM_U + 2 * c, g - k * stride[e]));
+          for (int k = 1; k <= 4; ++k)
+            acc += P.D[e][k - 1] * diff(get_pair(Qf, NG, PM_U + 2 * c, g + k * stride[e]),
+                                        get_pair(Qf, NG, PM_U + 2 * c, g - k * stride[e]));
+        }
         Gf[(size_t)(3 * e + c) * NG + g] = acc;
       }
     }
@@ -480,6 +485,7 @@ void launch_grad_m(const DevState &s, cudaStream_t st) {
   GradParamsM P;
   for (int d = 0; d < 3; ++d)
     for (int k = 0; k < 4; ++k) P.D[d][k] = (float)s.hcoef->D[d][k];
+  P.ihx = s.hcoef->D[0][0] * 1.25;
   k_grad_m<<<grid_for(s.nghost, 128), 128, 0, st>>>(s, P);
 }
 

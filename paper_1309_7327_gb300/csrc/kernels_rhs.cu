@@ -10,6 +10,7 @@
 //   k_final  pointwise: Y_k div V_c, h div V_c and rho*omega_k
 #include <cstdio>
 
+#include "bc.cuh"
 #include "chem.cuh"
 #include "smc_internal.h"
 
@@ -100,6 +101,7 @@ __global__ void __launch_bounds__(128) k_prim(const DevState s, const double *__
 // ---------------------------------------------------------------- k_grad
 struct GradParams {
   double D[3][4];
+  double ihx;                     // 1/h_x (boundary-lowered x derivatives)
 };
 
 __device__ __forceinline__ int find_box_g(const Box *__restrict__ b, int nb, long long g) {
@@ -126,14 +128,26 @@ __global__ void __launch_bounds__(128) k_grad(const DevState s, const GradParams
     const long long stride[3] = {1, B.gx, (long long)B.gx * B.gy};
     int nghost_dirs = 0;
     for (int e = 0; e < 3; ++e) nghost_dirs += (crd[e] < 0 || crd[e] >= n[e]);
+    // cells next to non-periodic x ends take the lowered x derivative
+    const int gxi = B.lo[0] + ix;
+    const int kb = !s.x_outflow ? -1
+                   : (gxi >= 0 && gxi < 4) ? gxi
+                   : (gxi >= s.nx_domain - 4 && gxi < s.nx_domain) ? s.nx_domain - 1 - gxi : -1;
     for (int e = 0; e < 3; ++e) {
       if (crd[e] < 0 || crd[e] >= n[e]) continue;   // D_e needs e-interior cells
       if (nghost_dirs > 1) continue;                // edges are never read
       for (int c = 0; c < 3; ++c) {
         double acc = 0.0;
+        if (e == 0 && kb >= 0) {
+          const long long sg = gxi < 4 ? 1 : -1;
+          double v[7];
+          for (int j = 0; j < 7; ++j) v[j] = QF(Q_U + c, g + sg * (j - kb));
+          acc = (double)sg * lowered_d(v, kb) * P.ihx;
+        } else {
 #pragma unroll
-        for (int k = 1; k <= 4; ++k)
-          acc += P.D[e][k - 1] * (QF(Q_U + c, g + k * stride[e]) - QF(Q_U + c, g - k * stride[e]));
+          for (int k = 1; k <= 4; ++k)
+            acc += P.D[e][k - 1] * (QF(Q_U + c, g + k * stride[e]) - QF(Q_U + c, g - k * stride[e]));
+        }
         s.G[(size_t)(3 * e + c) * NG + g] = acc;
       }
     }
@@ -463,6 +477,7 @@ void launch_grad(const DevState &s, cudaStream_t st) {
   const Coef *hc = s.hcoef;
   for (int d = 0; d < 3; ++d)
     for (int k = 0; k < 4; ++k) P.D[d][k] = hc->D[d][k];
+  P.ihx = hc->D[0][0] * 1.25;
   k_grad<<<grid_for(s.nghost, 128), 128, 0, st>>>(s, P);
 }
 

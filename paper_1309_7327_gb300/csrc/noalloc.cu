@@ -102,6 +102,8 @@ extern "C" smc_status smc_rhs_noalloc(const int n[3], const double dx[3],
   B.nx = n[0]; B.ny = n[1]; B.nz = n[2];
   B.gx = gx; B.gy = gy; B.gz = gz;
   B.off_g = 0; B.off_i = 0;
+  B.lo[0] = B.lo[1] = B.lo[2] = 0;
+  B.pad = 0;
   *reinterpret_cast<unsigned *>(hs + o_status) = 0u;   // the status word starts at zero
   int *gmap = reinterpret_cast<int *>(hs + o_gmap);
   long long *imap = reinterpret_cast<long long *>(hs + o_imap);

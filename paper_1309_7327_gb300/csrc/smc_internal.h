@@ -70,6 +70,16 @@ struct Box {
   int nx, ny, nz;
   int gx, gy, gz;                 // ghosted extents n + 8
   long long off_g, off_i;         // first ghosted / interior cell
+  int lo[3];                      // global index of the first interior cell
+  int pad;
+};
+
+// An interior cell within four cells of a non-periodic x end: its x-direction
+// terms use the boundary-lowered stencils (Sec. 2.2, boundary paragraph).
+struct BcCell {
+  long long g, i;                 // ghosted and interior index
+  int k;                          // distance from the end, 0..3
+  int side;                       // 0: low x end, 1: high x end
 };
 
 // One thread's share of a stencil direction: a segment of one grid line.
@@ -103,6 +113,18 @@ enum {
   Q_U = 0, Q_V, Q_W, Q_T, Q_P, Q_RHO, Q_RHOH, Q_C43, Q_ETA, Q_C23, Q_LAM,
   Q_HMIX, Q_AP, Q_SB, Q_KX, Q_KY, Q_KZ, Q_NBASE
 };
+// float-plane indices of the mixed-precision scratch (reuses the FP64 Q buffer)
+enum {
+  PM_U = 0, PM_V = 2, PM_W = 4, PM_T = 6, PM_P = 8, PM_KX = 10, PM_KY = 12, PM_KZ = 14,
+  PM_HMIX = 16, PM_RHO = 18, PM_RHOH = 20,
+  PM_C43 = 22, PM_ETA, PM_C23, PM_LAM, PM_AP, PM_SB, PM_NBASE
+};
+__host__ __device__ inline int pmY(int ns, int k) { return PM_NBASE + 2 * k; }
+__host__ __device__ inline int pmX(int ns, int k) { return PM_NBASE + 2 * ns + 2 * k; }
+__host__ __device__ inline int pmRY(int ns, int k) { return PM_NBASE + 4 * ns + 2 * k; }
+__host__ __device__ inline int pmRD(int ns, int k) { return PM_NBASE + 6 * ns + k; }
+__host__ __device__ inline int pmRDH(int ns, int k) { return PM_NBASE + 7 * ns + k; }
+__host__ __device__ inline int pmB(int ns, int k) { return PM_NBASE + 8 * ns + k; }
 // species blocks start at Q_NBASE: Y, X, rhoY, rhoD, rhoD*h', B
 inline __host__ __device__ int qY(int ns) { return Q_NBASE; }
 inline __host__ __device__ int qX(int ns) { return Q_NBASE + ns; }
@@ -143,7 +165,18 @@ struct DevState {
   unsigned *status;
   Opts opt;
   float xi_ratio_f;
+  int x_outflow;                  // 1: the x ends are non-periodic boundaries
+  int nx_domain;                  // cells of the domain along x
+  const BcCell *bc_cells;         // the cells next to the x ends (x_outflow only)
+  long long n_bc;
 };
+
+// Boundary-lowered x-direction terms at the cells next to the x ends; they
+// replace what the x line kernel stored there (FP64 result, or the float
+// accumulator of the mixed path).  Launch after the x-direction line kernel
+// and before the y and z ones.
+void launch_xbc(const DevState &s, double *dU, cudaStream_t st);
+void launch_xbc_m(const DevState &s, float *dUf, cudaStream_t st);
 
 void launch_prim(const DevState &s, const double *U, cudaStream_t st);
 void launch_grad(const DevState &s, cudaStream_t st);

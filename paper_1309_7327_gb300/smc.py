@@ -52,6 +52,9 @@ class smc_mechanism(C.Structure):
                 ("Pr", C.c_double)]
 
 
+SMC_BC_PERIODIC, SMC_BC_OUTFLOW = 0, 1
+
+
 class smc_bc(C.Structure):
     _fields_ = [("lo", C.c_int * 3), ("hi", C.c_int * 3)]
 
@@ -224,7 +227,10 @@ def _ptr(a):
 class Smc:
     """A library handle for one box layout and mechanism on the current GPU."""
 
-    def __init__(self, grid, mech, options: dict | None = None):
+    def __init__(self, grid, mech, options: dict | None = None, x_outflow: bool = False,
+                 bc: tuple | None = None):
+        """x_outflow: non-periodic x ends (boundary-lowered stencils).  bc:
+        explicit (lo[3], hi[3]) boundary kinds (SMC_BC_*), overriding it."""
         L = lib()
         self._keep = []
 
@@ -253,9 +259,14 @@ class Smc:
         m.Ea = arr(mech.Ea, np.float64)
         m.Le = arr(mech.Le, np.float64)
         m.eta_ref, m.T_ref, m.eta_exp, m.Pr = mech.eta_ref, mech.T_ref, mech.eta_exp, mech.Pr
-        bc = smc_bc()
+        b = smc_bc()
+        if bc is not None:
+            for d in range(3):
+                b.lo[d], b.hi[d] = int(bc[0][d]), int(bc[1][d])
+        elif x_outflow:
+            b.lo[0] = b.hi[0] = SMC_BC_OUTFLOW
         self.h = C.c_void_p()
-        st = L.smc_create(C.byref(g), C.byref(m), C.byref(bc), C.byref(self.h))
+        st = L.smc_create(C.byref(g), C.byref(m), C.byref(b), C.byref(self.h))
         self._keep = []
         if st != SMC_OK:
             msg = L.smc_last_error(self.h).decode() if self.h else ""

@@ -105,3 +105,19 @@ def test_create_rejects_bad_mechanism_without_touching_the_gpu(lib):
     with pytest.raises(smc.SmcError) as e:
         smc.Smc(g, m)
     assert e.value.status == smc.SMC_ERR_ARG and "mass" in str(e.value)
+
+
+def test_create_rejects_unsupported_boundaries_without_touching_the_gpu(lib):
+    """Non-periodic y or z faces, or mixed x faces, are refused during host
+    validation; outflow x needs at least 8 cells along x."""
+    from paper_1309_7327_gb300 import synth
+    m = synth.make_mechanism(3, 2, 1)
+    g = synth.single_box(8, 0.1)
+    P, O = smc.SMC_BC_PERIODIC, smc.SMC_BC_OUTFLOW
+    for bc in (((P, O, P), (P, O, P)), ((O, P, P), (P, P, P)), ((P, P, 7), (P, P, 7))):
+        with pytest.raises(smc.SmcError) as e:
+            smc.Smc(g, m, bc=bc)
+        assert e.value.status == smc.SMC_ERR_ARG and "boundar" in str(e.value)
+    with pytest.raises(smc.SmcError) as e:
+        smc.Smc(synth.single_box((6, 8, 8), 0.1), m, x_outflow=True)
+    assert "8 cells" in str(e.value)
