@@ -210,15 +210,17 @@ def cpu_baseline(wl, budget_s: float = 15.0):
     g = wl.grid
     prim = synth.boxes_to_global(g, wl.prim)
     U = thermo.conserved(prim, wl.mech.nasa7, wl.mech.W)
-    # one box's worth of cells, evaluated as a ghosted patch of the global field
+    # one box's worth of cells (at most 32 per axis), evaluated as a ghosted
+    # patch of the global field
     b = int(np.argmin([g.box_cells(i) for i in range(g.nboxes)]))
     (x0, y0, z0), (x1, y1, z1) = g.lo[b], g.hi[b]
+    x1, y1, z1 = min(x1, x0 + 31), min(y1, y0 + 31), min(z1, z0 + 31)
     nz, ny, nx = U.shape[1:]
     iz = np.arange(z0 - 4, z1 + 5) % nz
     iy = np.arange(y0 - 4, y1 + 5) % ny
     ix = np.arange(x0 - 4, x1 + 5) % nx
     patch = U[:, iz][:, :, iy][:, :, :, ix]
-    cells = g.box_cells(b)
+    cells = (x1 - x0 + 1) * (y1 - y0 + 1) * (z1 - z0 + 1)
     evals, t0 = 0, time.perf_counter()
     while True:
         orhs.rhs_ghosted(patch, wl.mech, g.dx)
@@ -228,7 +230,7 @@ def cpu_baseline(wl, budget_s: float = 15.0):
             break
     return {"value": cells * evals / el / 1e6, "unit": "Mcell-RHS/s", "cores": 1,
             "kind": "oracle",
-            "sample": f"{evals} full RHS evaluations of box {b} ({cells} cells) of workload "
+            "sample": f"{evals} full RHS evaluations of {cells} cells of box {b} of workload "
                       f"{wl.name} by the NumPy FP64 oracle, {el:.1f} s"}
 
 
@@ -290,7 +292,7 @@ def main():
         """Warm up, then time args.steps steps on device-resident state."""
         opts = variants[name]
         precision = opts["precision"]
-        h = smc.Smc(wl.grid, wl.mech, opts)
+        h = smc.Smc(wl.grid, wl.mech, opts, x_outflow=wl.x_outflow)
         stream = torch.cuda.Stream(device)
         h.set_stream(stream)
         prim = torch.from_numpy(wl.prim).to(device)
@@ -300,6 +302,22 @@ def main():
         h.synchronize()
         del prim
         U0 = U.clone()
+        def rhs_ms(reps=3):
+            """CUDA-event time of one full right-hand-side evaluation."""
+            F = torch.empty_like(U)
+            h.rhs(U, F)
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize(device)
+            a.record(stream)
+            for _ in range(reps):
+                h.rhs(U, F)
+            b.record(stream)
+            torch.cuda.synchronize(device)
+            del F
+            return a.elapsed_time(b) / reps
+
+        rhs_default = rhs_ms()                # the library's default schedule
         if args.tiles:                        # a fixed schedule (profiling runs)
             seg, xl, mv = (int(v) for v in args.tiles.split(","))
             h.set_option("segment", seg)
@@ -308,6 +326,7 @@ def main():
             tuned = {"segment": seg, "x_layout": xl, "march": mv if precision == 1 else 0}
         else:
             tuned = h.autotune(U)             # segment length, x-line layout, line kernel
+        tuned = dict(tuned, rhs_ms_default=rhs_default, rhs_ms_tuned=rhs_ms())
         for _ in range(args.warmup):          # also fills the recycled f(U_0)
             h.sdc_step(U, wl.dt, nodes, sweeps, rsub)
         h.synchronize()
@@ -337,9 +356,22 @@ def main():
         h.synchronize()
         st2 = h.stats()
         h.set_option("profile", 0)
+        # the same steps launched kernel by kernel (no graph replay), timed
+        # like the graph-replayed ones: what the graph capture saves
+        h.set_option("use_graphs", 0)
+        h.sdc_step(U, wl.dt, nodes, sweeps, rsub)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize(device)
+        e0.record(stream)
+        for _ in range(args.steps):
+            h.sdc_step(U, wl.dt, nodes, sweeps, rsub)
+        e1.record(stream)
+        torch.cuda.synchronize(device)
+        ms_eager = e0.elapsed_time(e1) / args.steps
         h.close()
         return dict(ms_step=ms / args.steps, launches=launches, kms=st2["kernel_ms"],
-                    clocks=clocks, U0=U0, tuned=tuned)
+                    clocks=clocks, U0=U0, tuned=tuned, ms_eager=ms_eager)
 
     runs = {}
     order = {"both": ["mixed", "fp64", "mixed_rates32"]}.get(args.precision, [args.precision])
@@ -405,6 +437,7 @@ def main():
         hbm = None
     precision_report = {k: {"value": world * ncells * evals_per_step / (r["ms_step"] / 1e3) / 1e6,
                             "ms_per_step": r["ms_step"], "autotuned": r["tuned"],
+                            "ms_per_step_without_graphs": r["ms_eager"],
                             "kernel_ms_per_step": {kk: vv / args.steps for kk, vv in r["kms"].items()}}
                         for k, r in runs.items()}
     if "mixed" in runs and "fp64" in runs:
@@ -417,7 +450,7 @@ def main():
     Uh = U0.cpu().numpy().copy()
     h2 = smc.Smc(wl.grid, wl.mech, dict(main_opts, segment=R["tuned"]["segment"],
                                         x_layout=R["tuned"]["x_layout"],
-                                        march=R["tuned"]["march"]))
+                                        march=R["tuned"]["march"]), x_outflow=wl.x_outflow)
     h2.sdc_step(Uh, wl.dt, nodes, sweeps, rsub)
     e2e_steps = max(1, min(args.steps, 3))
     t0 = time.perf_counter()

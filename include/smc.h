@@ -132,9 +132,11 @@ enum {
   SMC_OPT_X_LAYOUT = 13,       /* x-direction lines of the current precision: 0 read the box
                                   layout, 1 read an x-slowest copy (default 0 FP64, 1 mixed) */
   SMC_OPT_MARCH = 14,          /* stencil-line kernel of the current precision: 0 evaluates
-                                  every face from its 8-point window, 1 slides 9-cell register
-                                  windows along the line, one load per field and cell
-                                  (mixed only; default 0 FP64, 1 mixed) */
+                                  every face from its 8-point window; 1, 2, 3 slide 9-cell
+                                  register windows along the line, one load per field and
+                                  cell, in chunks of 16 / 32 / 16 cells sized for 3 / 3 / 4
+                                  resident blocks per SM (mixed only; default 0 FP64,
+                                  1 mixed) */
   SMC_OPT_RATES = 15,          /* production rates under SMC_OPT_PRECISION = 1: 0 (default)
                                   FP64 like the FP64 path; 1 FP32 mantissas after FP64 Gibbs
                                   energies, reaction exponents and exponent reductions

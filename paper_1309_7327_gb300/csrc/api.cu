@@ -360,7 +360,8 @@ smc_status eval_rhs(smc_handle *h, const double *U, double *F, int transport, in
     for (int d = 0; d < 3; ++d) {
       {
         Timed t(h, SMC_K_MARCH);
-        if (mixed && h->march[1]) launch_march_m2(d == 0 ? sx : s, d, h->d_dUf, d == 0, h->stream);
+        if (mixed && h->march[1])
+          launch_march_m2(d == 0 ? sx : s, d, h->d_dUf, d == 0, h->march[1], h->stream);
         else if (mixed) launch_march_m(d == 0 ? sx : s, d, h->d_dUf, d == 0, h->stream);
         else launch_march(d == 0 ? sx : s, d, F, d == 0, h->stream);
       }
@@ -1050,9 +1051,9 @@ smc_status smc_set_option(smc_handle *h, int key, double v) {
       h->xt[h->precision == 1] = (int)v;
       return SMC_OK;
     case SMC_OPT_MARCH:
-      if (v != 0.0 && v != 1.0) return fail(h, SMC_ERR_ARG, "march kernel must be 0 or 1");
-      if (v == 1.0 && h->precision != 1)
-        return fail(h, SMC_ERR_ARG, "the sliding-window line kernel is mixed precision only");
+      if (v < 0 || v > 3 || v != floor(v)) return fail(h, SMC_ERR_ARG, "march kernel must be 0..3");
+      if (v != 0.0 && h->precision != 1)
+        return fail(h, SMC_ERR_ARG, "the sliding-window line kernels are mixed precision only");
       h->march[h->precision == 1] = (int)v;
       return SMC_OK;
     case SMC_OPT_FINE_REPEAT:
@@ -1126,15 +1127,24 @@ smc_status smc_autotune(smc_handle *h, const double *U, int *segment, int *x_lay
   h->cache_kind = 0;   // slot 0 is overwritten
   const int mixed = h->precision == 1;
   const int segs[4] = {8, 16, 32, 64};
-  const int nvar = mixed ? 2 : 1;
+  const int nvar = mixed ? 4 : 1;
   float best = 1e30f;
   int best_seg = h->segment, best_xt = h->xt[mixed], best_mv = h->march[mixed];
   cudaEvent_t a, b;
   CUDA_TRY(h, cudaEventCreate(&a));
   CUDA_TRY(h, cudaEventCreate(&b));
+  // the x-slowest copy needs (nQ + 9) ghosted planes; try it only if that
+  // fits with room to spare
+  int nx_layouts = 2;
+  if (!h->d_Qt) {
+    size_t fr = 0, tot = 0;
+    const size_t need = ((size_t)nQ(h->ns) + 9) * (size_t)h->nghost * sizeof(double);
+    if (cudaMemGetInfo(&fr, &tot) != cudaSuccess || fr < need + (need >> 2) + (1ull << 30))
+      nx_layouts = 1;
+  }
   for (int mv = 0; mv < nvar; ++mv)
     for (int si = 0; si < 4; ++si)
-      for (int x = 0; x < 2; ++x) {
+      for (int x = 0; x < nx_layouts; ++x) {
         h->segment = segs[si];
         h->xt[mixed] = x;
         h->march[mixed] = mv;
@@ -1159,6 +1169,14 @@ smc_status smc_autotune(smc_handle *h, const double *U, int *segment, int *x_lay
   h->segment = best_seg;
   h->xt[mixed] = best_xt;
   h->march[mixed] = best_mv;
+  if (!h->xt[0] && !h->xt[1] && h->d_Qt) {
+    // the copy is not used: give its memory back
+    CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    cudaFree(h->d_Qt);
+    cudaFree(h->d_Gt);
+    h->d_Qt = h->d_Gt = nullptr;
+    h->dev_bytes -= (long long)(((size_t)nQ(h->ns) + 9) * (size_t)h->nghost * sizeof(double));
+  }
   if ((st = build_lines(h))) return st;
   h->opt_version++;
   if (segment) *segment = best_seg;

@@ -511,7 +511,7 @@ void launch_final_m(const DevState &s, const double *U, const float *dUf, double
 
 // ------------------------------------------------------------ k_march_m2
 // The same terms as k_march_m, organised for data reuse.  Each thread walks
-// its line segment in chunks of up to M2_CH cells.  Every field is held in a
+// its line segment in chunks of up to CH cells.  Every field is held in a
 // 9-cell register window (cells c-4 .. c+4 of the current cell c) that slides
 // by one cell per step, so a field value is loaded once per cell rather than
 // once per face or per stencil point.  The terms are taken in sub-passes over
@@ -519,7 +519,6 @@ void launch_final_m(const DevState &s, const double *U, const float *dUf, double
 // velocity, then one species at a time) to bound the live registers; the
 // per-cell energy, correction velocity, species divergence sum and species
 // narrow term are carried between sub-passes in shared memory.
-constexpr int M2_CH = 16;
 constexpr int M2_NT = 128;
 
 namespace m2 {
@@ -636,11 +635,18 @@ __device__ __forceinline__ f2 flux_E(const Win &x, int r) {
 
 }  // namespace m2
 
-template <int DIR>
-__global__ void __launch_bounds__(M2_NT, 3) k_march_m2(const DevState s, const MarchParamsM P,
-                                                       float *__restrict__ dUf, int first) {
+// CH: cells per chunk; MINB: resident blocks per SM the register budget is
+// sized for (3: 168 registers, 4: 128).  The four per-cell arrays live in
+// dynamic shared memory, 4 CH M2_NT floats.
+template <int DIR, int CH, int MINB>
+__global__ void __launch_bounds__(M2_NT, MINB) k_march_m2(const DevState s, const MarchParamsM P,
+                                                          float *__restrict__ dUf, int first) {
   using namespace m2;
-  __shared__ float sE[M2_CH][M2_NT], sV[M2_CH][M2_NT], sN[M2_CH][M2_NT], sO[M2_CH][M2_NT];
+  extern __shared__ float m2_smem[];
+  float(*sE)[M2_NT] = reinterpret_cast<float(*)[M2_NT]>(m2_smem);
+  float(*sV)[M2_NT] = sE + CH;
+  float(*sN)[M2_NT] = sV + CH;
+  float(*sO)[M2_NT] = sN + CH;
   const int tid = threadIdx.x;
   const long long item = blockIdx.x * (long long)blockDim.x + tid;
   if (item >= s.nlines[DIR]) return;   // no block-wide barrier below
@@ -656,8 +662,8 @@ __global__ void __launch_bounds__(M2_NT, 3) k_march_m2(const DevState s, const M
   x.NG = (size_t)s.nghost;
   x.sg = L.sg;
 
-  for (int c0 = 0; c0 < L.len; c0 += M2_CH) {
-    const int n = min(M2_CH, L.len - c0);
+  for (int c0 = 0; c0 < L.len; c0 += CH) {
+    const int n = min(CH, L.len - c0);
     x.gb = L.g0 + (long long)c0 * L.sg;
     const long long ib = L.i0 + (long long)c0 * L.si;
     for (int c = 0; c < n; ++c) {
@@ -964,7 +970,24 @@ __global__ void __launch_bounds__(M2_NT, 3) k_march_m2(const DevState s, const M
   }
 }
 
-void launch_march_m2(const DevState &s, int dir, float *dUf, int first, cudaStream_t st) {
+template <int CH, int MINB>
+static void launch_m2_variant(const DevState &s, int dir, const MarchParamsM &P, float *dUf,
+                              int first, int blocks, cudaStream_t st) {
+  const size_t smem = 4 * CH * M2_NT * sizeof(float);
+  static bool attr_set = false;     // once per instantiation, before any stream capture
+  if (!attr_set) {
+    cudaFuncSetAttribute(k_march_m2<0, CH, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(k_march_m2<1, CH, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(k_march_m2<2, CH, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    attr_set = true;
+  }
+  if (dir == 0) k_march_m2<0, CH, MINB><<<blocks, M2_NT, smem, st>>>(s, P, dUf, first);
+  else if (dir == 1) k_march_m2<1, CH, MINB><<<blocks, M2_NT, smem, st>>>(s, P, dUf, first);
+  else k_march_m2<2, CH, MINB><<<blocks, M2_NT, smem, st>>>(s, P, dUf, first);
+}
+
+void launch_march_m2(const DevState &s, int dir, float *dUf, int first, int variant,
+                     cudaStream_t st) {
   MarchParamsM P;
   for (int a = 0; a < 8; ++a)
     for (int b = 0; b < 8; ++b) P.M[a][b] = (float)s.hcoef->M[dir][a][b];
@@ -972,9 +995,9 @@ void launch_march_m2(const DevState &s, int dir, float *dUf, int first, cudaStre
   const long long n = s.nlines[dir];
   if (n == 0) return;
   const int blocks = (int)((n + M2_NT - 1) / M2_NT);
-  if (dir == 0) k_march_m2<0><<<blocks, M2_NT, 0, st>>>(s, P, dUf, first);
-  else if (dir == 1) k_march_m2<1><<<blocks, M2_NT, 0, st>>>(s, P, dUf, first);
-  else k_march_m2<2><<<blocks, M2_NT, 0, st>>>(s, P, dUf, first);
+  if (variant == 2) launch_m2_variant<32, 3>(s, dir, P, dUf, first, blocks, st);
+  else if (variant == 3) launch_m2_variant<16, 4>(s, dir, P, dUf, first, blocks, st);
+  else launch_m2_variant<16, 3>(s, dir, P, dUf, first, blocks, st);
 }
 
 }  // namespace smc

@@ -194,7 +194,10 @@ int nQm(int ns);
 void launch_prim_m(const DevState &s, const double *U, cudaStream_t st);
 void launch_grad_m(const DevState &s, cudaStream_t st);
 void launch_march_m(const DevState &s, int dir, float *dUf, int first, cudaStream_t st);
-void launch_march_m2(const DevState &s, int dir, float *dUf, int first, cudaStream_t st);
+// variant 1: 16-cell chunks, 3 blocks/SM; 2: 32-cell chunks, 3 blocks/SM;
+// 3: 16-cell chunks, 4 blocks/SM
+void launch_march_m2(const DevState &s, int dir, float *dUf, int first, int variant,
+                     cudaStream_t st);
 void launch_final_m(const DevState &s, const double *U, const float *dUf, double *dU, int transport,
                     int chemistry, cudaStream_t st);
 

@@ -387,6 +387,41 @@ def flame_fields(grid: Grid, ns: int, seed: int, Tu=300.0, Tb=2000.0,
     return prim
 
 
+def spectral_velocity(grid: Grid, seed: int, rms: float, slope: float = -5.0 / 3.0,
+                      kmin: int = 1, kmax: int | None = None) -> np.ndarray:
+    """A seeded random-phase solenoidal velocity field [3, nz, ny, nx] on the
+    periodic box with energy spectrum E(k) ~ k^slope on kmin <= |k| <= kmax
+    (mode numbers), scaled to the given rms (over the three components, one
+    factor, so the field stays divergence-free).  Fourier
+    amplitudes |u(k)| ~ sqrt(E(k) / (4 pi k^2)); the divergence-free part is
+    kept by projecting out k (k . u(k))/|k|^2."""
+    rng = np.random.default_rng(seed)
+    nx, ny, nz = grid.domain
+    kx = np.fft.fftfreq(nx, 1.0 / nx)
+    ky = np.fft.fftfreq(ny, 1.0 / ny)
+    kz = np.fft.rfftfreq(nz, 1.0 / nz)
+    KY, KX, KZ = np.meshgrid(ky, kx, kz, indexing="ij")    # [ny, nx, nz//2+1]
+    kmag = np.sqrt(KX ** 2 + KY ** 2 + KZ ** 2)
+    kmax = kmax or max(1, min(nx, ny, nz) // 4)
+    amp = np.zeros_like(kmag)
+    band = (kmag >= kmin) & (kmag <= kmax)
+    amp[band] = np.sqrt(kmag[band] ** slope / (4.0 * np.pi * kmag[band] ** 2))
+    uh = []
+    for _ in range(3):
+        ph = rng.uniform(0.0, 2.0 * np.pi, size=kmag.shape)
+        uh.append(amp * np.exp(1j * ph))
+    k2 = np.where(kmag > 0, kmag ** 2, 1.0)
+    div = (KX * uh[0] + KY * uh[1] + KZ * uh[2]) / k2
+    uh = [uh[0] - KX * div, uh[1] - KY * div, uh[2] - KZ * div]
+    out = np.empty((3, nz, ny, nx))
+    for c in range(3):
+        # the transform runs over [y][x][z]; the result is laid out [z][y][x]
+        f = np.fft.irfftn(uh[c], s=(ny, nx, nz), axes=(0, 1, 2))
+        out[c] = np.transpose(f, (2, 0, 1))
+    out *= rms / np.sqrt(np.mean(out ** 2))
+    return out
+
+
 # --------------------------------------------------------------------------
 # the workloads
 # --------------------------------------------------------------------------
@@ -403,6 +438,7 @@ class Workload:
     reaction_substeps: int
     steps: int
     precision: str
+    x_outflow: bool = False  # non-periodic x ends (boundary-lowered stencils)
 
 
 def _acoustic_dt(h: float, umax: float, Tmax: float, cfl: float = 0.5) -> float:
@@ -462,9 +498,12 @@ def workload(name: str, seed: int = 1, n: int | None = None) -> Workload:
         else:
             grid = single_box((2 * n, n, n), 1.0 / 256)
         mech = make_mechanism(21, 84, seed)
-        g = flame_fields(grid, 21, seed + 100, ubase=1000.0, pert=0.1)
-        dt = 0.5 * _acoustic_dt(grid.dx[0], 2000.0, 2000.0)
-        return Workload(name, grid, mech, global_to_boxes(grid, g), dt, 5, 8, 5, 50, "mixed")
+        g = flame_fields(grid, 21, seed + 100, ubase=0.0, pert=0.0)
+        # turbulent-like velocity: k^-5/3 spectrum, 10 m/s rms, over the flame
+        g[0:3] = spectral_velocity(grid, seed + 200, rms=1000.0)
+        dt = 0.5 * _acoustic_dt(grid.dx[0], 4000.0, 2000.0)
+        return Workload(name, grid, mech, global_to_boxes(grid, g), dt, 5, 8, 5, 50, "mixed",
+                        x_outflow=True)
     raise ValueError(f"unknown workload {name!r}")
 
 

@@ -204,11 +204,12 @@ def test_bad_arguments(smc):
 @pytest.mark.parametrize("precision", [0, 1])
 def test_tile_choices_give_identical_results_and_autotune(smc, precision):
     """Segment length and x-line layout change only the schedule: every
-    choice gives the same bits for a given line kernel; the two mixed line
-    kernels agree to the mixed tolerance; the autotuner picks one of the
-    choices."""
+    choice gives the same bits for a given line kernel (and the three
+    sliding-window variants the same bits as each other); the per-face and
+    sliding-window kernels agree to the mixed tolerance; the autotuner picks
+    one of the choices."""
     wl, U, U_g = state("c1", seed=7, p_amp=0.03)
-    marches = (0, 1) if precision else (0,)
+    marches = (0, 1, 2, 3) if precision else (0,)
     ref = {}
     for mv in marches:
         outs = []
@@ -222,6 +223,8 @@ def test_tile_choices_give_identical_results_and_autotune(smc, precision):
     if precision:
         assert relerr(ref[1], oracle_rhs(wl, U_g)).max() < TOL_MIXED
         assert relerr(ref[1], ref[0]).max() < TOL_MIXED
+        # the sliding-window variants differ only in chunking and occupancy
+        assert np.array_equal(ref[1], ref[2]) and np.array_equal(ref[1], ref[3])
     with smc.Smc(wl.grid, wl.mech, {"precision": precision}) as h:
         choice = h.autotune(dev(U))
         assert choice["segment"] in (8, 16, 32, 64) and choice["x_layout"] in (0, 1)

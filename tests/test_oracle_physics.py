@@ -196,3 +196,22 @@ def test_x_outflow_rhs_changes_only_the_cells_near_the_x_ends():
     uni = np.broadcast_to(U_g[:, :1, :1, :1], U_g.shape).copy()
     tr, _ = rhs.rhs_periodic(uni, wl.mech, wl.grid.dx, opt, parts=True)
     assert np.abs(tr).max() <= 1e-9 * np.abs(uni).max()
+
+
+def test_spectral_velocity_is_solenoidal_with_the_requested_spectrum():
+    """The scale configuration's velocity generator: divergence-free (in
+    Fourier space), the requested rms, and an energy spectrum of slope
+    -5/3 over the seeded band."""
+    g = synth.single_box((48, 48, 48), 1.0 / 256)
+    u = synth.spectral_velocity(g, 3, rms=1000.0, kmax=12)
+    assert abs(np.sqrt(np.mean(u ** 2)) - 1000.0) < 1e-9 * 1000.0
+    U = [np.fft.fftn(u[c]) for c in range(3)]
+    k = np.fft.fftfreq(48, 1.0 / 48)
+    KZ, KY, KX = np.meshgrid(k, k, k, indexing="ij")
+    div = KX * U[0] + KY * U[1] + KZ * U[2]
+    assert np.abs(div).max() < 1e-12 * np.abs(KX * U[0]).max()
+    km = np.rint(np.sqrt(KX ** 2 + KY ** 2 + KZ ** 2)).astype(int)
+    P = sum(np.abs(x) ** 2 for x in U)
+    E = np.array([P[km == kk].sum() for kk in range(2, 12)])
+    slope = np.polyfit(np.log(np.arange(2, 12)), np.log(E), 1)[0]
+    assert -1.9 < slope < -1.45, slope
