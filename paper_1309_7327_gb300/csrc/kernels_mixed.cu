@@ -747,6 +747,9 @@ __global__ void __launch_bounds__(M2_NT, MINB) k_march_m2(const DevState s, cons
       float H = ds(a, 0, w);
 #pragma unroll 1
       for (int c = 0; c < n; ++c) {
+        // the pressure part of the correction velocity,
+        // V_c,d = -(sum_l rhoD_l X_l,d + (sum_l B_l) p_d): p is in this pass's window
+        if (pass == 1 && mode == 0) sV[c][tid] = -x.s(PM_SB, c) * Dp(P, f);
         mv(P, f, 1, w);
         const float H2 = ds(a, 1, w);
         sE[c][tid] += H2 - H;
@@ -829,118 +832,82 @@ __global__ void __launch_bounds__(M2_NT, MINB) k_march_m2(const DevState s, cons
         }
       }
     }
-    // correction velocity V_c,d = -(sum_l rhoD_l X_l,d + (sum_l B_l) p_d)
-    if (mode == 0) {
-      {
-        f2 p[9];
-#pragma unroll
-        for (int i = 0; i < 9; ++i) p[i] = x.p(PM_P, i - 4);
+    // species, first pass: (rhoD_k X_k,d)_d, its energy part (rhoD_k h'_k X_k,d)_d
+    // and the species part of the correction velocity, -rhoD_k X_k,d; the
+    // narrow term goes straight to the accumulator
 #pragma unroll 1
-        for (int c = 0; c < n; ++c) {
-          sV[c][tid] = -x.s(PM_SB, c) * Dp(P, p);
-          if (c + 1 < n) {
-            slide(p);
-            p[8] = x.p(PM_P, c + 5);
-          }
-        }
+    for (int k = 0; k < ns; ++k) {
+      if (mode == 1 && k == ref) {
+        if (st)
+          for (int c = 0; c < n; ++c) put(dUf, NI, 5 + k, ib + (long long)c * L.si, 0.0f, true);
+        continue;
       }
-#pragma unroll 1
-      for (int l = 0; l < ns; ++l) {
-        f2 X[9];
+      f2 X[9];
+      float rd[9], rdh[9];
 #pragma unroll
-        for (int i = 0; i < 9; ++i) X[i] = x.p(pmX(ns, l), i - 4);
+      for (int i = 0; i < 9; ++i) {
+        X[i] = x.p(pmX(ns, k), i - 4);
+        rd[i] = x.s(pmRD(ns, k), i - 4);
+        rdh[i] = x.s(pmRDH(ns, k), i - 4);
+      }
+      float w[8];
+      mv(P, X, 0, w);
+      float H = ds(rd, 0, w), He = ds(rdh, 0, w);
 #pragma unroll 1
-        for (int c = 0; c < n; ++c) {
-          sV[c][tid] -= x.s(pmRD(ns, l), c) * Dp(P, X);
-          if (c + 1 < n) {
-            slide(X);
-            X[8] = x.p(pmX(ns, l), c + 5);
-          }
+      for (int c = 0; c < n; ++c) {
+        if (mode == 0) sV[c][tid] -= rd[4] * Dp(P, X);
+        mv(P, X, 1, w);
+        const float H2 = ds(rd, 1, w), He2 = ds(rdh, 1, w);
+        put(dUf, NI, 5 + k, ib + (long long)c * L.si, H2 - H, st);
+        sN[c][tid] += H2 - H;
+        sE[c][tid] += He2 - He;
+        H = H2;
+        He = He2;
+        if (c + 1 < n) {
+          slide(X); slide(rd); slide(rdh);
+          X[8] = x.p(pmX(ns, k), c + 5);
+          rd[8] = x.s(pmRD(ns, k), c + 5);
+          rdh[8] = x.s(pmRDH(ns, k), c + 5);
         }
       }
     }
-    // species, one at a time
+    // species, second pass (V_c complete): (B_k p_d)_d, -D_d(rho Y_k u_d) and
+    // Y_k,d V_c,d
 #pragma unroll 1
     for (int k = 0; k < ns; ++k) {
       const bool narrow = !(mode == 1 && k == ref);
-      if (narrow) {
-        // (rhoD_k X_k,d)_d and its energy part (rhoD_k h'_k X_k,d)_d
-        {
-          f2 X[9];
-          float rd[9], rdh[9];
+      f2 p[9], Fk[9], Yk[9];
+      float B[9];
 #pragma unroll
-          for (int i = 0; i < 9; ++i) {
-            X[i] = x.p(pmX(ns, k), i - 4);
-            rd[i] = x.s(pmRD(ns, k), i - 4);
-            rdh[i] = x.s(pmRDH(ns, k), i - 4);
-          }
-          float w[8];
-          mv(P, X, 0, w);
-          float H = ds(rd, 0, w), He = ds(rdh, 0, w);
-#pragma unroll 1
-          for (int c = 0; c < n; ++c) {
-            mv(P, X, 1, w);
-            const float H2 = ds(rd, 1, w), He2 = ds(rdh, 1, w);
-            sO[c][tid] = H2 - H;
-            sE[c][tid] += He2 - He;
-            H = H2;
-            He = He2;
-            if (c + 1 < n) {
-              slide(X); slide(rd); slide(rdh);
-              X[8] = x.p(pmX(ns, k), c + 5);
-              rd[8] = x.s(pmRD(ns, k), c + 5);
-              rdh[8] = x.s(pmRDH(ns, k), c + 5);
-            }
-          }
-        }
-        // (B_k p_d)_d
-        {
-          f2 p[9];
-          float B[9];
-#pragma unroll
-          for (int i = 0; i < 9; ++i) {
-            p[i] = x.p(PM_P, i - 4);
-            B[i] = x.s(pmB(ns, k), i - 4);
-          }
-          float w[8];
-          mv(P, p, 0, w);
-          float H = ds(B, 0, w);
-#pragma unroll 1
-          for (int c = 0; c < n; ++c) {
-            mv(P, p, 1, w);
-            const float H2 = ds(B, 1, w);
-            const float o = sO[c][tid] + (H2 - H);
-            sO[c][tid] = o;
-            sN[c][tid] += o;
-            H = H2;
-            if (c + 1 < n) {
-              slide(p); slide(B);
-              p[8] = x.p(PM_P, c + 5);
-              B[8] = x.s(pmB(ns, k), c + 5);
-            }
-          }
-        }
+      for (int i = 0; i < 9; ++i) {
+        p[i] = x.p(PM_P, i - 4);
+        B[i] = x.s(pmB(ns, k), i - 4);
+        Fk[i] = mul(x.p(pmRY(ns, k), i - 4), x.p(PM_U + 2 * DIR, i - 4));
+        if (mode == 0) Yk[i] = x.p(pmY(ns, k), i - 4);
       }
-      // -D_d(rho Y_k u_d) and Y_k,d V_c,d
-      {
-        f2 Fk[9], Yk[9];
-#pragma unroll
-        for (int i = 0; i < 9; ++i) {
-          Fk[i] = mul(x.p(pmRY(ns, k), i - 4), x.p(PM_U + 2 * DIR, i - 4));
-          if (mode == 0) Yk[i] = x.p(pmY(ns, k), i - 4);
-        }
+      float w[8];
+      mv(P, p, 0, w);
+      float H = ds(B, 0, w);
 #pragma unroll 1
-        for (int c = 0; c < n; ++c) {
-          float o = (narrow ? sO[c][tid] : 0.0f) - Dp(P, Fk);
-          if (mode == 0) o = fmaf(Dp(P, Yk), sV[c][tid], o);
-          put(dUf, NI, 5 + k, ib + (long long)c * L.si, o, st);
-          if (c + 1 < n) {
-            slide(Fk);
-            Fk[8] = mul(x.p(pmRY(ns, k), c + 5), x.p(PM_U + 2 * DIR, c + 5));
-            if (mode == 0) {
-              slide(Yk);
-              Yk[8] = x.p(pmY(ns, k), c + 5);
-            }
+      for (int c = 0; c < n; ++c) {
+        float o = -Dp(P, Fk);
+        if (mode == 0) o = fmaf(Dp(P, Yk), sV[c][tid], o);
+        if (narrow) {
+          mv(P, p, 1, w);
+          const float H2 = ds(B, 1, w);
+          o += H2 - H;
+          sN[c][tid] += H2 - H;
+          H = H2;
+        }
+        put(dUf, NI, 5 + k, ib + (long long)c * L.si, o, false);
+        if (c + 1 < n) {
+          slide(p); slide(B); slide(Fk);
+          p[8] = x.p(PM_P, c + 5);
+          B[8] = x.s(pmB(ns, k), c + 5);
+          Fk[8] = mul(x.p(pmRY(ns, k), c + 5), x.p(PM_U + 2 * DIR, c + 5));
+          if (mode == 0) {
+            slide(Yk);
+            Yk[8] = x.p(pmY(ns, k), c + 5);
           }
         }
       }
