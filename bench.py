@@ -408,6 +408,18 @@ def main():
             "traffic": traffic_db.get(f"k_march:{main_key}:{args.workload}"),
             "peak_source": f"{src}: 152 SMs x FMA/clk x median SM clock under load",
             "share": kms["march"] / max(sum(kms.values()), 1e-9)}
+        # the same kernel against HBM: algorithmic bytes = every primitive
+        # plane read once over the ghosted cells plus the accumulator written
+        # once over the interior cells
+        esize, planes = (8, 17 + 6 * wl.mech.ns) if main_opts["precision"] == 0 else \
+            (4, 28 + 9 * wl.mech.ns)
+        ghosted = sum((wl.grid.box_shape(b)[0] + 8) * (wl.grid.box_shape(b)[1] + 8)
+                      * (wl.grid.box_shape(b)[2] + 8) for b in range(wl.grid.nboxes))
+        mbytes = planes * esize * ghosted + nv * esize * ncells
+        hbm_peak_m = measured_peaks().get("hbm_gbs", 6800.0)
+        rooflines["k_march"]["hbm"] = {
+            "algorithmic_bytes": mbytes, "achieved_gbs": mbytes / (march_ms / 1e3) / 1e9,
+            "peak_gbs": hbm_peak_m, "frac": mbytes / (march_ms / 1e3) / 1e9 / hbm_peak_m}
     n_fine = launches["fine"]
     if n_fine:
         per = rsub - 1
