@@ -602,10 +602,14 @@ __device__ __forceinline__ float Ds(const MarchParamsM &P, const float *w) {
   return acc;
 }
 
+// Store, or add without waiting for the old value: the add goes out as a
+// reduction (no result returned), so the thread does not stall on a global
+// load in every step of the march.  Each cell is updated by one thread per
+// launch, in program order, so the sums are deterministic.
 __device__ __forceinline__ void put(float *__restrict__ dUf, size_t NI, int comp, long long i, float v,
                                     bool store) {
   float *q = dUf + (size_t)comp * NI + i;
-  if (store) *q = v; else *q += v;
+  if (store) *q = v; else atomicAdd(q, v);
 }
 
 // transverse momentum fluxes rho u_d u_t - eta u_d,t (t = e, f) at window offset r
