@@ -204,6 +204,7 @@ __global__ void __launch_bounds__(128) k_grad_m(const DevState s, const GradPara
 struct MarchParamsM {
   float M[8][8];
   float D[4];
+  float2 MT2[8][4];               // (M[2j][t], M[2j+1][t]): two rows of a column, for FFMA2
 };
 
 // w[m] = sum_{n != 3} M[m][n] (x_n - x_3) for a window of float pairs
@@ -543,45 +544,75 @@ struct Win {
   }
 };
 
-// v[n] = sum_m a[o+m] M[m][n] for n != 3
+// v[n] = sum_m a[o+m] M[m][n] for n != 3, two columns per paired FMA
 __device__ __forceinline__ void vm(const MarchParamsM &P, const float *a, int o, float *v) {
 #pragma unroll
-  for (int nn = 0; nn < 8; ++nn) {
-    float acc = 0.0f;
+  for (int np = 0; np < 4; ++np) {
+    float2 acc = make_float2(0.0f, 0.0f);
 #pragma unroll
-    for (int mm = 0; mm < 8; ++mm)
-      if (nn != 3 && mm - nn <= 4 && nn - mm <= 4) acc = fmaf(a[o + mm], P.M[mm][nn], acc);
-    v[nn] = acc;
+    for (int mm = 0; mm < 8; ++mm) {
+      const int n0 = 2 * np, n1 = 2 * np + 1;
+      const bool nz = (mm - n0 <= 4 && n0 - mm <= 4) || (mm - n1 <= 4 && n1 - mm <= 4);
+      if (nz)
+        acc = __ffma2_rn(make_float2(a[o + mm], a[o + mm]),
+                         make_float2(P.M[mm][n0], P.M[mm][n1]), acc);
+    }
+    v[2 * np] = acc.x;
+    v[2 * np + 1] = acc.y;
   }
 }
-// w[m] = sum_{n != 3} M[m][n] (x[o+n] - x[o+3])
+// the differences x[o+t] - x[o+3] of a pair window, one paired add each
+__device__ __forceinline__ void diffs(const f2 *x, int o, float *d) {
+  const float2 m3 = make_float2(-x[o + 3].h, -x[o + 3].l);
+#pragma unroll
+  for (int t = 0; t < 8; ++t) {
+    if (t == 3) {
+      d[t] = 0.0f;
+    } else {
+      const float2 e = __fadd2_rn(make_float2(x[o + t].h, x[o + t].l), m3);
+      d[t] = e.x + e.y;
+    }
+  }
+}
+// w[m] = sum_{n != 3} M[m][n] (x[o+n] - x[o+3]), two rows per paired FMA
 __device__ __forceinline__ void mv(const MarchParamsM &P, const f2 *x, int o, float *w) {
   float d[8];
+  diffs(x, o, d);
+  float2 acc[4];
 #pragma unroll
-  for (int t = 0; t < 8; ++t) d[t] = (t == 3) ? 0.0f : diff(x[o + t], x[o + 3]);
+  for (int j = 0; j < 4; ++j) acc[j] = make_float2(0.0f, 0.0f);
 #pragma unroll
-  for (int mm = 0; mm < 8; ++mm) {
-    float acc = 0.0f;
+  for (int t = 0; t < 8; ++t) {
+    if (t == 3) continue;
+    const float2 dd = make_float2(d[t], d[t]);
 #pragma unroll
-    for (int t = 0; t < 8; ++t)
-      if (t != 3 && mm - t <= 4 && t - mm <= 4) acc = fmaf(P.M[mm][t], d[t], acc);
-    w[mm] = acc;
+    for (int j = 0; j < 4; ++j) {
+      const int m0 = 2 * j, m1 = 2 * j + 1;
+      const bool nz = (m0 - t <= 4 && t - m0 <= 4) || (m1 - t <= 4 && t - m1 <= 4);
+      if (nz) acc[j] = __ffma2_rn(P.MT2[t][j], dd, acc[j]);
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    w[2 * j] = acc[j].x;
+    w[2 * j + 1] = acc[j].y;
   }
 }
 // sum_{n != 3} v[n] (x[o+n] - x[o+3])
 __device__ __forceinline__ float dp(const float *v, const f2 *x, int o) {
-  float acc = 0.0f;
+  float d[8];
+  diffs(x, o, d);
+  float2 acc = make_float2(0.0f, 0.0f);
 #pragma unroll
-  for (int t = 0; t < 8; ++t)
-    if (t != 3) acc = fmaf(v[t], diff(x[o + t], x[o + 3]), acc);
-  return acc;
+  for (int t = 0; t < 8; t += 2) acc = __ffma2_rn(make_float2(v[t], v[t + 1]), make_float2(d[t], d[t + 1]), acc);
+  return acc.x + acc.y;
 }
 // sum_t a[o+t] w[t]
 __device__ __forceinline__ float ds(const float *a, int o, const float *w) {
-  float acc = 0.0f;
+  float2 acc = make_float2(0.0f, 0.0f);
 #pragma unroll
-  for (int t = 0; t < 8; ++t) acc = fmaf(a[o + t], w[t], acc);
-  return acc;
+  for (int t = 0; t < 8; t += 2) acc = __ffma2_rn(make_float2(a[o + t], a[o + t + 1]), make_float2(w[t], w[t + 1]), acc);
+  return acc.x + acc.y;
 }
 template <typename T>
 __device__ __forceinline__ void slide(T *w) {
@@ -963,6 +994,8 @@ void launch_march_m2(const DevState &s, int dir, float *dUf, int first, int vari
   for (int a = 0; a < 8; ++a)
     for (int b = 0; b < 8; ++b) P.M[a][b] = (float)s.hcoef->M[dir][a][b];
   for (int k = 0; k < 4; ++k) P.D[k] = (float)s.hcoef->D[dir][k];
+  for (int t = 0; t < 8; ++t)
+    for (int j = 0; j < 4; ++j) P.MT2[t][j] = make_float2(P.M[2 * j][t], P.M[2 * j + 1][t]);
   const long long n = s.nlines[dir];
   if (n == 0) return;
   const int blocks = (int)((n + M2_NT - 1) / M2_NT);
