@@ -145,13 +145,17 @@ enum {
                                   this many consecutive groups of reaction_substeps
                                   Gauss-Lobatto nodes; 1 (default) is type (b), more is
                                   type (c) (1..8; at most 64 fine intervals per step) */
-  SMC_OPT_SDC_EXIT = 17        /* eps >= 0; 0 (default) runs every sweep.  eps > 0: after each
+  SMC_OPT_SDC_EXIT = 17,       /* eps >= 0; 0 (default) runs every sweep.  eps > 0: after each
                                   sweep compute the residual R^k = U_0 + dt q.F^k - U_M^k of
                                   eq. residual (for MRSDC the coarse and fine quadratures of
                                   f1 and f2) and end the step once |R^(k-1)| / |R^k| < 1 + eps
                                   or |R^k| = 0.  Reads the residual to the host every sweep
                                   (a stream synchronisation); steps are then launched one
                                   kernel at a time, not replayed as a graph */
+  SMC_OPT_CHAIN_BLOCKS = 18    /* cap on the resident blocks per SM of the multirate reaction
+                                  chain, 0 (default) = the hardware limit; 1..16 reserve
+                                  unused shared memory to enforce it (fewer resident threads,
+                                  more L1 per thread for the chain's local arrays) */
 };
 
 /* Kernel classes counted in smc_stats (launches always; times only while

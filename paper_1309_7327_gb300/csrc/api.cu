@@ -760,6 +760,7 @@ smc_status smc_create(const smc_grid *grid, const smc_mechanism *mech, const smc
   h->opt.tol = 1e-13;
   h->opt.T0 = 1000.0;
   h->opt.xi_ratio = 0.0;
+  h->opt.chain_blocks = 0;
   build_coef(h);
   cudaGetDevice(&h->device);
   // ---- device memory
@@ -1059,6 +1060,10 @@ smc_status smc_set_option(smc_handle *h, int key, double v) {
     case SMC_OPT_FINE_REPEAT:
       if (v < 1 || v > 8 || v != floor(v)) return fail(h, SMC_ERR_ARG, "fine repeat must be 1..8");
       h->fine_repeat = (int)v;
+      return SMC_OK;
+    case SMC_OPT_CHAIN_BLOCKS:
+      if (v < 0 || v > 16 || v != floor(v)) return fail(h, SMC_ERR_ARG, "chain blocks must be 0..16");
+      h->opt.chain_blocks = (int)v;
       return SMC_OK;
     case SMC_OPT_SDC_EXIT:
       if (!(v >= 0.0) || !std::isfinite(v)) return fail(h, SMC_ERR_ARG, "sdc exit must be >= 0");

@@ -23,12 +23,26 @@ struct f2 {
 };
 
 // x = hi + lo with hi the truncation of x to 24 bits (exactly representable)
-// and lo the remainder truncated to 24 bits: about 48 significant bits, one
-// FP64 operation.
+// and lo the remainder truncated to 24 bits: about 48 significant bits.  In
+// integer arithmetic only (the FP64 pipe is the scarce one): hi keeps the
+// top 23 stored mantissa bits; lo is the low 29 bits, x - hi exactly,
+// normalised and truncated to a float.  Zero, subnormal and tiny remainders
+// flush to zero, as trunc_float does.
 __device__ __forceinline__ void put_pair(float *Qf, size_t NG, int plane, long long g, double x) {
-  const double hd = __longlong_as_double(__double_as_longlong(x) & (long long)0xFFFFFFFFE0000000ULL);
-  Qf[(size_t)plane * NG + g] = trunc_float(hd);
-  Qf[(size_t)(plane + 1) * NG + g] = trunc_float(x - hd);
+  const long long b = __double_as_longlong(x);
+  Qf[(size_t)plane * NG + g] = trunc_float(__longlong_as_double(b & (long long)0xFFFFFFFFE0000000ULL));
+  const unsigned m = (unsigned)(b & 0x1FFFFFFFLL);                 // x - hi = m 2^(e - 52)
+  const int e = (int)((b >> 52) & 0x7ff) - 1023;
+  float lo = 0.0f;
+  if (m != 0u && e > -1022 && e < 1024) {
+    const int p = 31 - __clz(m);                                    // leading bit of m, 0..28
+    const int fe = e - 52 + p + 127;                                // float exponent field
+    if (fe > 0) {
+      const unsigned frac = (p >= 23 ? (m >> (p - 23)) : (m << (23 - p))) & 0x7fffffu;
+      lo = __uint_as_float((unsigned)((unsigned long long)b >> 63) << 31 | (unsigned)fe << 23 | frac);
+    }
+  }
+  Qf[(size_t)(plane + 1) * NG + g] = lo;
 }
 
 __device__ __forceinline__ f2 get_pair(const float *__restrict__ Qf, size_t NG, int plane,

@@ -254,10 +254,24 @@ void launch_exp(const Mech *m, const double *x, double *y, long long n, cudaStre
   k_exp<<<grid_for(n, 256), 256, 0, st>>>(m, x, y, n);
 }
 
+// The chain's per-thread arrays (state, rates, Gibbs terms) live in local
+// memory; capping the resident blocks per SM (by reserving shared memory the
+// kernel does not use) trades FP64 latency hiding for L1 hits on them.
 void launch_fine_chain(const DevState &s, const double *Uin, double *Uout, const FineChain &fc,
                        cudaStream_t st) {
-  if (s.opt.rates32) k_fine_chain<true><<<grid_for(s.ncells, 128), 128, 0, st>>>(s, Uin, Uout, fc);
-  else k_fine_chain<false><<<grid_for(s.ncells, 128), 128, 0, st>>>(s, Uin, Uout, fc);
+  size_t smem = 0;
+  if (s.opt.chain_blocks > 0) {
+    smem = (size_t)(227 * 1024) / (size_t)s.opt.chain_blocks;
+    smem = smem > 1024 ? smem - 1024 : 0;
+    static bool attr_set = false;   // once, before any stream capture
+    if (!attr_set) {
+      cudaFuncSetAttribute(k_fine_chain<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+      cudaFuncSetAttribute(k_fine_chain<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+      attr_set = true;
+    }
+  }
+  if (s.opt.rates32) k_fine_chain<true><<<grid_for(s.ncells, 128), 128, smem, st>>>(s, Uin, Uout, fc);
+  else k_fine_chain<false><<<grid_for(s.ncells, 128), 128, smem, st>>>(s, Uin, Uout, fc);
 }
 
 }  // namespace smc

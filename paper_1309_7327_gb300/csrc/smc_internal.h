@@ -98,6 +98,7 @@ struct Opts {
   int reactions;
   int maxit;
   int rates32;                    // 1: production rates with FP32 mantissas (mixed precision only)
+  int chain_blocks;               // cap on resident reaction-chain blocks per SM (0: none)
   double tol, T0, xi_ratio;
 };
 

@@ -28,7 +28,7 @@ STATUS_NAMES = {0: "SMC_OK", 1: "SMC_ERR_ARG", 2: "SMC_ERR_CUDA", 3: "SMC_ERR_OO
 OPT = dict(precision=0, m47=1, m48=2, diffusion_mode=3, ref_species=4, xi_ratio=5,
            newton_tol=6, newton_maxit=7, t_guess=8, reactions=9, segment=10, profile=11,
            use_graphs=12, x_layout=13, march=14, rates=15,
-           fine_repeat=16, sdc_exit=17)
+           fine_repeat=16, sdc_exit=17, chain_blocks=18)
 KERNELS = ["prim", "grad", "march", "final", "update", "fine", "chem", "other"]
 
 EXPORTS = ["smc_create", "smc_destroy", "smc_rhs", "smc_sdc_step", "smc_prim_to_cons", "smc_autotune",
