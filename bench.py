@@ -65,6 +65,13 @@ def dist_setup(args):
     return world, rank, local
 
 
+def job_throughput(world, ncells, evals_per_step, ms_per_step):
+    """Whole-job Mcell-RHS/s: every rank advances its own replica of the
+    workload, so the job processes world x ncells x evals cells per step in
+    the slowest rank's step time."""
+    return world * ncells * evals_per_step / (ms_per_step / 1e3) / 1e6
+
+
 def barrier(world):
     if world > 1:
         import torch.distributed as dist
@@ -234,13 +241,33 @@ def cpu_baseline(wl, budget_s: float = 15.0):
                       f"{wl.name} by the NumPy FP64 oracle, {el:.1f} s"}
 
 
+def bench_config(wl, args, main_key, world):
+    """The workload description both arms print."""
+    nodes, sweeps, rsub = wl.nodes, wl.sweeps, wl.reaction_substeps
+    M1 = nodes - 1
+    per = rsub - 1 if rsub >= 2 else 0
+    ncells, nv = wl.grid.ncells, 5 + wl.mech.ns
+    return {"workload": args.workload + (f" (n={args.n})" if args.n else ""),
+            "boxes": wl.grid.nboxes, "cells": ncells,
+            "species": wl.mech.ns, "reactions": wl.mech.nr,
+            "boundaries": "x outflow, y z periodic" if wl.x_outflow else "periodic",
+            "integrator": (f"MRSDC {nodes} coarse / {rsub} fine GL, {sweeps} sweeps"
+                           if rsub >= 2 else f"SDC {nodes} GL, {sweeps} sweeps"),
+            "rhs_evals_per_step": sweeps * M1,
+            "reaction_evals_per_step": sweeps * M1 * per if per else 0,
+            "precision": PRECISION_TEXT[main_key],
+            "l2": "inputs larger than L2 (state %.0f MB)" % (nv * ncells * 8 / 1e6),
+            "parallelism": "replicas" if world > 1 else "single GPU"}
+
+
 def run_reference(args):
     """The oracle on the host cores (reference arm)."""
     world, rank, local = int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")), 0
     if rank != 0:
         return
     from paper_1309_7327_gb300 import synth
-    wl = synth.workload(args.workload, seed=args.seed)
+    wl = synth.workload(args.workload, seed=args.seed, n=args.n)
+    main_key = {"both": "mixed"}.get(args.precision, args.precision)
     for _ in range(args.warmup):
         cpu_baseline(wl, budget_s=1.0)
     vals = []
@@ -256,7 +283,7 @@ def run_reference(args):
             "warmup": args.warmup, "ms_per_step": 1000 * el / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64",
-            "data": "synthetic", "config": {"workload": args.workload},
+            "data": "synthetic", "config": bench_config(wl, args, main_key, world),
             "cpu_baseline": dict(last, value=value),
             "e2e": {"value": value, "unit": "Mcell-RHS/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
@@ -380,7 +407,7 @@ def main():
     main_key = order[0]
     R = runs[main_key]
     ms_step, launches, kms, clocks, U0 = R["ms_step"], R["launches"], R["kms"], R["clocks"], R["U0"]
-    value = world * ncells * evals_per_step / (ms_step / 1e3) / 1e6
+    value = job_throughput(world, ncells, evals_per_step, ms_step)
     main_opts = variants[main_key]
 
     # rooflines of the two heaviest kernels; "roofline" is the one with the
@@ -482,15 +509,7 @@ def main():
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64" if main_key == "fp64" else "f32+f64",
             "data": "synthetic",
-            "config": {"workload": args.workload + (f" (n={args.n})" if args.n else ""), "boxes": wl.grid.nboxes, "cells": ncells,
-                       "species": wl.mech.ns, "reactions": wl.mech.nr,
-                       "integrator": (f"MRSDC {nodes} coarse / {rsub} fine GL, {sweeps} sweeps"
-                                      if rsub >= 2 else f"SDC {nodes} GL, {sweeps} sweeps"),
-                       "rhs_evals_per_step": evals_per_step,
-                       "reaction_evals_per_step": sweeps * M1 * per if per else 0,
-                       "precision": PRECISION_TEXT[main_key],
-                       "l2": "inputs larger than L2 (state %.0f MB)" % (nv * ncells * 8 / 1e6),
-                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "config": bench_config(wl, args, main_key, world),
             "roofline": roofline, "rooflines": rooflines, "hbm": hbm, "cpu_baseline": cpu, "e2e": e2e,
             "precisions": precision_report,
             "gpu_launches": int(sum(launches.values())),
