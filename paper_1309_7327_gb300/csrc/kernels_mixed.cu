@@ -990,12 +990,16 @@ template <int CH, int MINB>
 static void launch_m2_variant(const DevState &s, int dir, const MarchParamsM &P, float *dUf,
                               int first, int blocks, cudaStream_t st) {
   const size_t smem = 4 * CH * M2_NT * sizeof(float);
-  static bool attr_set = false;     // once per instantiation, before any stream capture
-  if (!attr_set) {
+  // the attribute is per device: set it once per device and instantiation,
+  // on the first (eager) launch, before any stream capture
+  static bool attr_set[64] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev >= 0 && dev < 64 && !attr_set[dev]) {
     cudaFuncSetAttribute(k_march_m2<0, CH, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     cudaFuncSetAttribute(k_march_m2<1, CH, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     cudaFuncSetAttribute(k_march_m2<2, CH, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    attr_set = true;
+    attr_set[dev] = true;
   }
   if (dir == 0) k_march_m2<0, CH, MINB><<<blocks, M2_NT, smem, st>>>(s, P, dUf, first);
   else if (dir == 1) k_march_m2<1, CH, MINB><<<blocks, M2_NT, smem, st>>>(s, P, dUf, first);

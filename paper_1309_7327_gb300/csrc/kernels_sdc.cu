@@ -263,11 +263,13 @@ void launch_fine_chain(const DevState &s, const double *Uin, double *Uout, const
   if (s.opt.chain_blocks > 0) {
     smem = (size_t)(227 * 1024) / (size_t)s.opt.chain_blocks;
     smem = smem > 1024 ? smem - 1024 : 0;
-    static bool attr_set = false;   // once, before any stream capture
-    if (!attr_set) {
+    static bool attr_set[64] = {};  // per device, on the first (eager) launch
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev >= 0 && dev < 64 && !attr_set[dev]) {
       cudaFuncSetAttribute(k_fine_chain<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
       cudaFuncSetAttribute(k_fine_chain<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-      attr_set = true;
+      attr_set[dev] = true;
     }
   }
   if (s.opt.rates32) k_fine_chain<true><<<grid_for(s.ncells, 128), 128, smem, st>>>(s, Uin, Uout, fc);
