@@ -159,6 +159,9 @@ def smc_heat2d(N, h, a, b, G, u, t0, dt, nsteps, m47=3557.0 / 44100.0, m48=-2083
     """Advance the App. A heat problem in place (see smc.h); a, b, G (or
     None), u: CUDA float64 tensors of N*N elements.  Returns the number of
     operator evaluations."""
+    for arr in (a, b, G, u):
+        if arr is not None and arr.numel() != int(N) * int(N):
+            raise ValueError(f"heat arrays need {int(N) * int(N)} values")
     ev = C.c_longlong(0)
     raw = getattr(stream, "cuda_stream", stream)
     st = lib().smc_heat2d(int(N), float(h), _ptr(a), _ptr(b), _ptr(G) if G is not None else None,
@@ -172,6 +175,8 @@ def smc_heat2d(N, h, a, b, G, u, t0, dt, nsteps, m47=3557.0 / 44100.0, m48=-2083
 def smc_exp(x, y):
     """y = exp(x) elementwise by the library's exponential (CUDA float64
     tensors of equal size); synchronous."""
+    if y.numel() < x.numel():
+        raise ValueError("y is smaller than x")
     st = lib().smc_exp(_ptr(x), _ptr(y), C.c_longlong(x.numel()))
     if st != SMC_OK:
         raise SmcError(st, "smc_exp")
@@ -199,6 +204,10 @@ def smc_rhs_noalloc(n, dx, mech, U, dUdt, stream=None):
     nn = (C.c_int * 3)(*[int(v) for v in n])
     dd = (C.c_double * 3)(*[float(v) for v in dx])
     raw = getattr(stream, "cuda_stream", stream)
+    need = (5 + mech.ns) * int(n[0]) * int(n[1]) * int(n[2])
+    for arr in (U, dUdt):
+        if arr.numel() != need:
+            raise ValueError(f"expected {need} values, got {arr.numel()}")
     st = lib().smc_rhs_noalloc(nn, dd, C.byref(m), _ptr(U), _ptr(dUdt), C.c_void_p(raw))
     if st != SMC_OK:
         raise SmcError(st, "smc_rhs_noalloc")
@@ -294,24 +303,33 @@ class Smc:
         raw = getattr(stream, "cuda_stream", stream)
         self._check(lib().smc_set_stream(self.h, C.c_void_p(raw)))
 
+    def _state(self, a):
+        """The pointer of a state-shaped array: NV x cells float64 (the C ABI
+        takes raw pointers and cannot check sizes itself)."""
+        n = a.numel() if hasattr(a, "numel") else a.size
+        if n != self.nv * self.ncells:
+            raise ValueError(f"expected {self.nv} x {self.ncells} values, got {n}")
+        return _ptr(a)
+
     def rhs(self, U, out):
-        self._check(lib().smc_rhs(self.h, _ptr(U), _ptr(out)))
+        self._check(lib().smc_rhs(self.h, self._state(U), self._state(out)))
         return out
 
     def sdc_step(self, U, dt, nodes=3, sweeps=4, reaction_substeps=0):
-        self._check(lib().smc_sdc_step(self.h, _ptr(U), float(dt), nodes, sweeps,
+        self._check(lib().smc_sdc_step(self.h, self._state(U), float(dt), nodes, sweeps,
                                        reaction_substeps))
         return U
 
     def prim_to_cons(self, prim, out):
-        self._check(lib().smc_prim_to_cons(self.h, _ptr(prim), _ptr(out)))
+        self._check(lib().smc_prim_to_cons(self.h, self._state(prim), self._state(out)))
         return out
 
     def autotune(self, U) -> dict:
         """Pick the fastest stencil segment length, x-line layout and line
         kernel at U."""
         seg, xl, mv = C.c_int(), C.c_int(), C.c_int()
-        self._check(lib().smc_autotune(self.h, _ptr(U), C.byref(seg), C.byref(xl), C.byref(mv)))
+        self._check(lib().smc_autotune(self.h, self._state(U), C.byref(seg), C.byref(xl),
+                                       C.byref(mv)))
         return {"segment": seg.value, "x_layout": xl.value, "march": mv.value}
 
     def synchronize(self):
