@@ -129,8 +129,9 @@ enum {
   SMC_OPT_USE_GRAPHS = 12,     /* 1 (default): replay recycled steps as one CUDA graph when the
                                   handle has a non-default stream and profiling is off; 0: launch
                                   kernels one by one */
-  SMC_OPT_X_LAYOUT = 13,       /* x-direction lines of the current precision: 0 read the box
-                                  layout, 1 read an x-slowest copy (default 0 FP64, 1 mixed) */
+  SMC_OPT_X_LAYOUT = 13,       /* x-direction lines of the current precision: 0 (default) read
+                                  the box layout, 1 read an x-slowest copy made once per
+                                  evaluation (nQ + 9 more ghosted planes of device memory) */
   SMC_OPT_MARCH = 14,          /* stencil-line kernel of the current precision: 0 evaluates
                                   every face from its 8-point window; 1, 2, 3 slide 9-cell
                                   register windows along the line, one load per field and

@@ -24,7 +24,7 @@ struct smc_handle {
   Opts opt;
   int precision = 0;
   int segment = 16;
-  int xt[2] = {0, 1};                   // x lines on the x-slowest copy (FP64, mixed)
+  int xt[2] = {0, 0};                   // x lines on the x-slowest copy (FP64, mixed)
   int march[2] = {0, 1};                // stencil-line kernel (FP64, mixed)
   int rates32 = 0;                      // FP32-mantissa production rates (mixed only)
   int fine_repeat = 1;                  // groups of fine nodes per coarse interval (type (c) if > 1)
