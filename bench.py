@@ -319,6 +319,7 @@ def main():
         """Warm up, then time args.steps steps on device-resident state."""
         opts = variants[name]
         precision = opts["precision"]
+        torch.cuda.empty_cache()              # earlier variants' tensors
         h = smc.Smc(wl.grid, wl.mech, opts, x_outflow=wl.x_outflow)
         stream = torch.cuda.Stream(device)
         h.set_stream(stream)
@@ -328,7 +329,8 @@ def main():
             h.prim_to_cons(prim, U)
         h.synchronize()
         del prim
-        U0 = U.clone()
+        torch.cuda.empty_cache()              # the library allocates with cudaMalloc
+        U0 = U.cpu()                          # the initial state, kept on the host
         def rhs_ms(reps=3):
             """CUDA-event time of one full right-hand-side evaluation."""
             F = torch.empty_like(U)
@@ -342,6 +344,7 @@ def main():
             b.record(stream)
             torch.cuda.synchronize(device)
             del F
+            torch.cuda.empty_cache()
             return a.elapsed_time(b) / reps
 
         rhs_default = rhs_ms()                # the library's default schedule
