@@ -50,6 +50,10 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
     ap.add_argument("--tiles", default=None,
                     help="segment,x_layout,march: use this stencil schedule instead of autotuning")
+    ap.add_argument("--fine-repeat", type=int, default=1,
+                    help="multirate fine-node groups per coarse interval (1: type (b), >1: type (c))")
+    ap.add_argument("--sdc-exit", type=float, default=0.0,
+                    help="residual early-exit threshold (0: every sweep runs)")
     return ap.parse_args()
 
 
@@ -251,10 +255,12 @@ def bench_config(wl, args, main_key, world):
             "boxes": wl.grid.nboxes, "cells": ncells,
             "species": wl.mech.ns, "reactions": wl.mech.nr,
             "boundaries": "x outflow, y z periodic" if wl.x_outflow else "periodic",
-            "integrator": (f"MRSDC {nodes} coarse / {rsub} fine GL, {sweeps} sweeps"
-                           if rsub >= 2 else f"SDC {nodes} GL, {sweeps} sweeps"),
+            "integrator": ((f"MRSDC {nodes} coarse / {rsub} fine GL"
+                            + (f" x {args.fine_repeat} (type c)" if args.fine_repeat > 1 else " (type b)")
+                            + f", {sweeps} sweeps") if rsub >= 2 else f"SDC {nodes} GL, {sweeps} sweeps")
+                           + (f", residual exit eps = {args.sdc_exit}" if args.sdc_exit > 0 else ""),
             "rhs_evals_per_step": sweeps * M1,
-            "reaction_evals_per_step": sweeps * M1 * per if per else 0,
+            "reaction_evals_per_step": sweeps * M1 * per * max(args.fine_repeat, 1) if per else 0,
             "precision": PRECISION_TEXT[main_key],
             "l2": "inputs larger than L2 (state %.0f MB)" % (nv * ncells * 8 / 1e6),
             "parallelism": "replicas" if world > 1 else "single GPU"}
@@ -290,10 +296,62 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+def run_heat(args):
+    """The App. A heat problems (T1/T2) through smc_heat2d: narrow stencil and
+    SDC (3 Gauss-Lobatto nodes, 4 sweeps) on an N x N periodic grid."""
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1309_7327_gb300 import smc, synth
+    N = args.n or 4096
+    f = synth.heat_fields(args.workload.upper(), N)
+    dev = torch.device("cuda", 0)
+    t = lambda x: torch.from_numpy(np.ascontiguousarray(x)).to(dev)        # noqa: E731
+    a, b, u = t(f["a"]), t(f["b"]), t(f["u0"])
+    G = t(f["G"]) if f["G"] is not None else None
+    h = f["h"]
+    # the App. A stability rule, dt0 = 0.4 / ((dx^-2 + dy^-2) max(a, b))
+    dt = 0.4 / ((2.0 / h ** 2) * max(float(f["a"].max()), float(f["b"].max())))
+    smc.smc_heat2d(N, h, a, b, G, u, 0.0, dt, args.warmup)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    sampler = ClockSampler(0)
+    sampler.start()
+    e0.record()
+    nev = smc.smc_heat2d(N, h, a, b, G, u, 0.0, dt, args.steps)
+    e1.record()
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1)
+    evals = nev - 1                            # the first call of each run evaluates F(U_0)
+    value = N * N * evals / (ms / 1e3) / 1e6
+    arrays = 5 if G is not None else 4         # a, b, u (, G) read and F written per evaluation
+    per_step = 8 * arrays * 8 + 8 * 7 * 8      # evaluations + node updates (5 F sources, U in, U out)
+    bytes_ = N * N * per_step * args.steps
+    peak = measured_peaks().get("hbm_gbs", 6800.0)
+    line = {"metric": f"Mcell-RHS/s (heat {args.workload.upper()})", "value": value,
+            "unit": "Mcell-RHS/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "grid": f"{N}x{N} periodic",
+                       "integrator": "SDC 3 GL, 4 sweeps", "stencil": "8th-order narrow (SMC)",
+                       "l2": "state and coefficients larger than L2 (%.0f MB)" % (N * N * 8 * 5 / 1e6)},
+            "roofline": {"bound": "hbm", "kernel": "whole step (k_heat_rhs + k_combo)",
+                         "achieved": bytes_ / (ms / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
+                         "frac": bytes_ / (ms / 1e3) / 1e9 / peak, "traffic": None},
+            "clocks": clocks, "gpu_launches": int(2 * evals)}
+    print(json.dumps(line))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.workload in ("t1", "t2"):
+        run_heat(args)
         return
     import numpy as np
     import torch
@@ -314,6 +372,11 @@ def main():
 
     variants = {"fp64": {"precision": 0}, "mixed": {"precision": 1},
                 "mixed_rates32": {"precision": 1, "rates": 1}}
+    for v in variants.values():
+        if args.fine_repeat > 1:
+            v["fine_repeat"] = args.fine_repeat
+        if args.sdc_exit > 0:
+            v["sdc_exit"] = args.sdc_exit
 
     def measure(name: str):
         """Warm up, then time args.steps steps on device-resident state."""
@@ -378,6 +441,7 @@ def main():
         ms = max_over_ranks(world, t_start.elapsed_time(t_end), device)
         st = h.stats()
         launches = {k: st["launches"][k] - base["launches"][k] for k in st["launches"]}
+        evals_done = (st["n_rhs"] - base["n_rhs"]) / args.steps      # RHS evaluations per step
         # the same steps again with every launch timed by CUDA events (eager
         # launches): per-kernel durations for the rooflines
         h.set_option("profile", 1)
@@ -401,7 +465,7 @@ def main():
         ms_eager = e0.elapsed_time(e1) / args.steps
         h.close()
         return dict(ms_step=ms / args.steps, launches=launches, kms=st2["kernel_ms"],
-                    clocks=clocks, U0=U0, tuned=tuned, ms_eager=ms_eager)
+                    clocks=clocks, U0=U0, tuned=tuned, ms_eager=ms_eager, evals=evals_done)
 
     runs = {}
     order = {"both": ["mixed", "fp64", "mixed_rates32"]}.get(args.precision, [args.precision])
@@ -410,6 +474,8 @@ def main():
     main_key = order[0]
     R = runs[main_key]
     ms_step, launches, kms, clocks, U0 = R["ms_step"], R["launches"], R["kms"], R["clocks"], R["U0"]
+    if args.sdc_exit > 0:                     # sweeps end early: count what ran
+        evals_per_step = R["evals"]
     value = job_throughput(world, ncells, evals_per_step, ms_step)
     main_opts = variants[main_key]
 
