@@ -556,6 +556,7 @@ def main():
 
     # end to end: host buffers through the C ABI, copies inside the timed region
     Uh = U0.cpu().numpy().copy()
+    torch.cuda.empty_cache()                  # the measured runs' tensors
     h2 = smc.Smc(wl.grid, wl.mech, dict(main_opts, segment=R["tuned"]["segment"],
                                         x_layout=R["tuned"]["x_layout"],
                                         march=R["tuned"]["march"]), x_outflow=wl.x_outflow)

@@ -88,8 +88,11 @@ def test_heat_T2_matches_oracle(smc):
 def test_heat_rejects_bad_arguments(smc):
     f = synth.heat_fields("T2", 16)
     a, u = dev(f["a"]), dev(f["u0"])
+    a4, u4 = a.flatten()[:16].contiguous(), u.flatten()[:16].contiguous()
     with pytest.raises(smc.SmcError):
-        smc.smc_heat2d(4, f["h"], a, a, None, u, 0.0, 0.1, 1)          # N < 8
+        smc.smc_heat2d(4, f["h"], a4, a4, None, u4, 0.0, 0.1, 1)       # N < 8
+    with pytest.raises(ValueError):
+        smc.smc_heat2d(8, f["h"], a, a, None, u, 0.0, 0.1, 1)          # arrays of another size
     with pytest.raises(smc.SmcError):
         smc.smc_heat2d(16, f["h"], a.cpu(), a, None, u, 0.0, 0.1, 1)   # host array
     assert smc.smc_heat2d(16, f["h"], a, a, None, u, 0.0, 0.1, 0) == 1  # no steps: F(U_0) only
