@@ -248,3 +248,93 @@ def mrsdc_step(U0, f1, f2, dt: float, coarse: int = 3, fine: int = 5, repeat: in
             if stop_rule(history, eps):
                 break
     return U, F1old[M1], F2old[M2], n1, n2
+
+
+def mrsdc2_step(U0, fA, fR, integrate, dt: float, coarse: int = 3, fine: int = 5,
+                repeat: int = 1, sweeps: int = 4, FA0=None, FR0=None, species=None):
+    """One mode-2 MRSDC step (eq. mrupdate2): the reactions R are the coarse
+    component (nodes t1), advection-diffusion A the fine one (nodes t2,
+    forward-Euler substeps).  Returns (U_new, A(U_new), R(U_new), n_A, n_R).
+
+    The coarse term is held at the right coarse node p + 1 of the interval
+    and is implicit.  Reading of "computed with VODE": the reaction ODE of
+    the interval, dU/dtau = R(U) + G (`integrate(U_p, G, dt_p)`, G constant),
+    is integrated from U^{k+1}_p with the BDF method, and its mean reaction
+    rate Rt = (U*(dt_p) - U_p)/dt_p - G (species components) stands for
+    f_slow(U^{k+1}_{p+1}); Rt^k (the previous sweep's) for f_slow(U^k_{p+1}).
+    Per coarse interval p of a sweep:
+
+    1. G1 = (dt/dt_p) sum_{q in p} [(S21 F1^k)_q + (S22 F2^k)_q] - Rt^k_{p+1}
+       (the terms of the summed fine updates known before the interval's
+       sweep); Rt' from integrate(U_p, G1, dt_p);
+    2. the fine substeps of eq. mrupdate2 with f_slow(U^{k+1}_{p+1}) = Rt',
+       which give A(U^{k+1}_q) at the interval's fine nodes;
+    3. G2 = G1 + (1/dt_p) sum_q dt_q [A(U^{k+1}_q) - A^k_q];
+       U^{k+1}_{p+1} = integrate(U_p, G2, dt_p) and Rt^{k+1}_{p+1} its mean
+       rate: the end value satisfies eq. mrupdate2 summed over the interval
+       with every term of this sweep, the stiff reaction term implicitly;
+    4. F1^{k+1}_{p+1} = R(U^{k+1}_{p+1}) (true R at the coarse node, for the
+       next sweep's quadrature S21 F1).
+
+    At a fixed point Rt' = Rt^{k+1} = Rt^k, the substeps of 2 end where 3
+    does, and U is the multirate collocation solution.  Spread start:
+    Rt^0 = F1^0 = R(U_0), F2^0 = A(U_0).  Taking the end value from the
+    fine substeps instead (one integration per interval) is not stable once
+    the reaction time scale is far below dt_p: the advection corrections
+    would then enter the end value explicitly, next to a stiff R.
+
+    fR returns full-size arrays (zero outside the species components);
+    `species` is the index (slice or mask) of those components, used to
+    zero Rt outside them."""
+    t1, t2, S21, S22 = mr_matrices(coarse, fine, repeat)
+    M1, M2 = coarse - 1, t2.shape[0] - 1
+    per = M2 // M1
+    dtq = dt * np.diff(t2)
+    nA = nR = 0
+    if FA0 is None:
+        FA0 = fA(U0)
+        nA += 1
+    if FR0 is None:
+        FR0 = fR(U0)
+        nR += 1
+    F1old = [FR0] * (M1 + 1)             # true R at the coarse nodes
+    Rtold = [FR0] * (M1 + 1)             # interval-mean R at the coarse nodes 1..M1
+    F2old = [FA0] * (M2 + 1)             # A at the fine nodes
+
+    def mean_rate(Up, G, dtp):
+        Us = integrate(Up, G, dtp)
+        Rt = (Us - Up) / dtp - G
+        if species is not None:
+            mask = np.zeros(Rt.shape[0], dtype=bool)
+            mask[species] = True
+            Rt[~mask] = 0.0
+        return Us, Rt
+
+    U = U0
+    for _ in range(sweeps):
+        F1new = [FR0] + [None] * M1
+        Rtnew = [None] * (M1 + 1)
+        F2new = [FA0] + [None] * M2
+        U = U0
+        for p in range(M1):
+            qs = range(p * per, (p + 1) * per)
+            dtp = dt * (t1[p + 1] - t1[p])
+            S = {q: dt * sum(S21[q, j] * F1old[j] for j in range(M1 + 1))
+                 + dt * sum(S22[q, j] * F2old[j] for j in range(M2 + 1) if S22[q, j] != 0.0)
+                 for q in qs}
+            G1 = sum(S[q] for q in qs) / dtp - Rtold[p + 1]
+            _, Rt1 = mean_rate(U, G1, dtp)
+            W = U
+            for q in qs:
+                if q > 0:
+                    F2new[q] = fA(W)
+                    nA += 1
+                W = (W + dtq[q] * (Rt1 - Rtold[p + 1]) + dtq[q] * (F2new[q] - F2old[q]) + S[q])
+            G2 = G1 + sum(dtq[q] * (F2new[q] - F2old[q]) for q in qs) / dtp
+            U, Rtnew[p + 1] = mean_rate(U, G2, dtp)
+            F1new[p + 1] = fR(U)
+            nR += 1
+        F2new[M2] = fA(U)
+        nA += 1
+        F1old, F2old, Rtold = F1new, F2new, Rtnew
+    return U, F2old[M2], F1old[M1], nA, nR

@@ -224,3 +224,109 @@ def test_mrsdc_residual_exit_reaches_the_multirate_collocation_solution():
                                       sweeps=60)
     assert len(hist) < 60 and hist[-1] < 1e-14
     assert abs(U[0] - Uref[0]) < 1e-15
+
+
+# ------------------------------------------------------------ mode 2 (eq. mrupdate2)
+
+def _linear_exact_integrate(r):
+    """U(dt) of U' = r U + G (closed form)."""
+    def integ(U, G, dt):
+        return (U + G / r) * math.exp(r * dt) - G / r
+    return integ
+
+
+def _mr2_collocation(u0, a, r, dt, coarse, fine):
+    """Mode-2 multirate collocation solution of u' = a u + r u: the
+    advection-like term a u on the fine nodes (S22), r u on the coarse ones
+    (S21), solved as one linear system."""
+    t1, t2, S21, S22 = sdc.mr_matrices(coarse, fine)
+    M1, M2 = coarse - 1, t2.shape[0] - 1
+    per = M2 // M1
+    A = np.zeros((M2 + 1, M2 + 1))
+    b = np.zeros(M2 + 1)
+    A[0, 0] = 1.0
+    b[0] = u0
+    for q in range(M2):
+        A[q + 1, q + 1] += 1.0
+        A[q + 1, q] -= 1.0
+        for j in range(M1 + 1):
+            A[q + 1, j * per] -= dt * S21[q, j] * r
+        for t in range(M2 + 1):
+            A[q + 1, t] -= dt * S22[q, t] * a
+    return np.linalg.solve(A, b)[-1]
+
+
+@pytest.mark.parametrize("coarse,fine", [(3, 3), (3, 5), (5, 3)])
+def test_mrsdc2_fixed_point_is_the_multirate_collocation_solution(coarse, fine):
+    """Iterated to convergence on u' = a u + r u (a on the fine nodes, r on
+    the coarse ones, the coarse term integrated exactly over each interval)
+    mode 2 reaches the multirate collocation solution."""
+    a, r, dt, u0 = -1.3, -4.0, 0.3, 1.7
+    ref = _mr2_collocation(u0, a, r, dt, coarse, fine)
+    U, _, _, _, _ = sdc.mrsdc2_step(np.array([u0]), lambda u: a * u, lambda u: r * u,
+                                    _linear_exact_integrate(r), dt, coarse=coarse, fine=fine,
+                                    sweeps=60)
+    assert abs(U[0] - ref) < 1e-13
+    # and it is a 2 M1-order approximation of exp((a + r) dt), not that value
+    assert abs(ref - u0 * math.exp((a + r) * dt)) < 1e-2 * u0
+
+
+def test_mrsdc2_order_equals_sweeps():
+    """u' = r u - u^2 (the logistic equation, closed form) with the linear
+    term on the coarse nodes: 4 sweeps, 3 coarse nodes give 4th order, 2
+    sweeps 2nd order."""
+    r, u0, T = -3.0, 1.0, 1.0
+    exact = r / (1.0 + (r / u0 - 1.0) * math.exp(-r * T))
+    for sweeps, order in ((4, 4), (2, 2)):
+        errs = []
+        for n in (8, 16, 32):
+            u = np.array([u0])
+            dt = T / n
+            for _ in range(n):
+                u, _, _, _, _ = sdc.mrsdc2_step(u, lambda x: -x * x, lambda x: r * x,
+                                                _linear_exact_integrate(r), dt, coarse=3,
+                                                fine=3, sweeps=sweeps)
+            errs.append(abs(u[0] - exact))
+        rates = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
+        assert min(rates) > order - 0.4, (sweeps, errs, rates)
+
+
+def test_mrsdc2_is_stable_where_mode1_is_not():
+    """A stiff coarse term, r dt_p = -100: mode 2 integrates it implicitly and
+    its sweeps settle on the collocation solution; mode 1 (the same term
+    explicit on the fine nodes) blows up."""
+    r, dt, u0 = -2e3, 0.1, 1.0
+    A = lambda x: -x * x + 1.0                                 # noqa: E731
+    R = lambda x: r * x                                        # noqa: E731
+    integ = _linear_exact_integrate(r)
+    U = {}
+    for sweeps in (12, 30, 60):
+        U[sweeps], _, _, _, _ = sdc.mrsdc2_step(np.array([u0]), A, R, integ, dt, coarse=3,
+                                                fine=3, sweeps=sweeps)
+    assert np.isfinite(U[60][0]) and abs(U[60][0]) < 2.0
+    assert abs(U[30][0] - U[60][0]) < 1e-9
+    assert abs(U[12][0] - U[60][0]) < 1e-3
+    with np.errstate(all="ignore"):
+        U1, _, _, _, _ = sdc.mrsdc_step(np.array([u0]), A, R, dt, coarse=3, fine=3, sweeps=4)
+    assert not np.isfinite(U1[0]) or abs(U1[0]) > 1e6
+
+
+def test_mrsdc2_with_the_bdf_integrator_matches_exact_integration():
+    """The BDF integrator in place of the closed form changes a mode-2 step
+    by no more than its tolerance (stiff coarse term)."""
+    from oracle import bdf
+    r, dt, u0 = -2e3, 0.05, 1.0
+    A = lambda x: -x * x + 1.0                                 # noqa: E731
+    R = lambda x: r * x                                        # noqa: E731
+
+    def integ_bdf(U, G, dtp):
+        f = lambda t, y: r * y + G                             # noqa: E731
+        jac = lambda t, y: (r * y + G, np.array([[r]]))        # noqa: E731
+        y, _ = bdf.bdf_integrate(f, jac, dtp, U, np.array([1e-14]), 1e-10)
+        return y
+
+    ex, _, _, _, _ = sdc.mrsdc2_step(np.array([u0]), A, R, _linear_exact_integrate(r), dt,
+                                     coarse=3, fine=3, sweeps=4)
+    bd, _, _, _, _ = sdc.mrsdc2_step(np.array([u0]), A, R, integ_bdf, dt, coarse=3, fine=3,
+                                     sweeps=4)
+    assert abs(bd[0] - ex[0]) < 1e-8 * abs(ex[0]) + 1e-13
