@@ -153,10 +153,21 @@ enum {
                                   or |R^k| = 0.  Reads the residual to the host every sweep
                                   (a stream synchronisation); steps are then launched one
                                   kernel at a time, not replayed as a graph */
-  SMC_OPT_CHAIN_BLOCKS = 18    /* cap on the resident blocks per SM of the multirate reaction
+  SMC_OPT_CHAIN_BLOCKS = 18,   /* cap on the resident blocks per SM of the multirate reaction
                                   chain, 0 (default) = the hardware limit; 1..16 reserve
                                   unused shared memory to enforce it (fewer resident threads,
                                   more L1 per thread for the chain's local arrays) */
+  SMC_OPT_MR_MODE = 19,        /* multirate mode of smc_sdc_step with reaction_substeps >= 2:
+                                  1 (default) explicit reactions on the fine nodes (eq.
+                                  mrupdate); 2 reactions on the coarse nodes, integrated
+                                  implicitly over each coarse interval by the BDF method,
+                                  advection-diffusion on the fine nodes (eq. mrupdate2;
+                                  at most 32 species) */
+  SMC_OPT_BDF_RTOL = 20,       /* relative tolerance of the implicit reaction integration,
+                                  0 < rtol < 1, default 1e-8 */
+  SMC_OPT_BDF_ATOL = 21        /* absolute tolerance of the implicit reaction integration in
+                                  mass-fraction units (the weight of rho Y_k is
+                                  atol rho + rtol |rho Y_k|), >= 0, default 1e-12 */
 };
 
 /* Kernel classes counted in smc_stats (launches always; times only while
@@ -170,7 +181,8 @@ enum {
   SMC_K_FINE = 5,       /* multirate fine-node reaction chain */
   SMC_K_CHEM = 6,       /* reaction-only evaluation */
   SMC_K_OTHER = 7,      /* primitive-to-conserved conversion, layout copies */
-  SMC_NKERNELS = 8
+  SMC_K_BDF = 8,        /* implicit reaction integration (MRSDC mode 2) */
+  SMC_NKERNELS = 9
 };
 
 typedef struct {
@@ -187,6 +199,13 @@ typedef struct {
   double residual[64];       /* |R^k| after sweep k of the last step (SMC_OPT_SDC_EXIT > 0
                                 only; 0 otherwise): max over components of
                                 max|R_c| / max|U_0,c| */
+  /* implicit reaction integration (SMC_OPT_MR_MODE 2, smc_react_integrate),
+     summed over every cell and call since the handle was created */
+  long long bdf_steps;       /* accepted BDF steps */
+  long long bdf_rejected;    /* steps rejected by the local error test */
+  long long bdf_newton_failures;   /* attempts whose Newton iteration failed */
+  long long bdf_evals;       /* production-rate evaluations */
+  long long bdf_max_steps;   /* most accepted steps of one cell in one call */
 } smc_stats;
 
 /* Create a handle: validates the mechanism (limits above) and the grid,
@@ -212,10 +231,16 @@ smc_status smc_rhs(smc_handle *h, const double *U, double *dUdt);
  *     Gauss-Lobatto nodes (3 or 5) and `sweeps` (>= 1) sweeps from the spread
  *     initial guess; f(U_0) is recycled from the previous step when U is the
  *     array the previous call left (call smc_invalidate after changing U).
- *   reaction_substeps = Y >= 2: multirate SDC mode 1, eq. mrupdate: `nodes`
- *     coarse Gauss-Lobatto nodes for advection-diffusion and Y Gauss-Lobatto
- *     fine nodes in every coarse interval (type (b), Sec. 3.2) for the
- *     reactions, Y <= 9. */
+ *   reaction_substeps = Y >= 2: multirate SDC, `nodes` coarse Gauss-Lobatto
+ *     nodes and Y Gauss-Lobatto fine nodes in every coarse interval (type (b),
+ *     Sec. 3.2; type (c) with SMC_OPT_FINE_REPEAT), Y <= 9.  Mode 1
+ *     (SMC_OPT_MR_MODE, default; eq. mrupdate): advection-diffusion on the
+ *     coarse nodes, explicit reactions on the fine nodes.  Mode 2 (eq.
+ *     mrupdate2): reactions on the coarse nodes, integrated implicitly over
+ *     every coarse interval (as smc_react_integrate, with the forcing of the
+ *     sweep's other terms), advection-diffusion on the fine nodes with
+ *     forward-Euler substeps; at most 10 fine intervals per coarse interval
+ *     and 32 species. */
 smc_status smc_sdc_step(smc_handle *h, double *U, double dt, int nodes,
                         int sweeps, int reaction_substeps);
 
@@ -308,6 +333,24 @@ smc_status smc_heat2d(int N, double h, const double *a, const double *b, const d
  * [-708, 709].  Synchronous; returns SMC_ERR_ARG for null arrays or
  * host pointers, SMC_ERR_CUDA if the launch fails. */
 smc_status smc_exp(const double *x, double *y, long long n);
+
+/* Implicit integration of the reactions alone, cell by cell (the coarse
+ * reaction term of MRSDC mode 2, eq. mrupdate2):
+ *   dU/dtau = R(U) + G,  U(0) = U,  0 <= tau <= dt,
+ * R the production rates of the species components (no other component
+ * has a reaction source), G a constant forcing (NULL: zero).  The
+ * non-species components move linearly; the species are integrated by a
+ * variable-order (1..5), variable-step BDF method with a Newton iteration on
+ * the analytic Jacobian at fixed density and internal energy, error
+ * weights SMC_OPT_BDF_ATOL rho + SMC_OPT_BDF_RTOL |rho Y_k|.  U, G and
+ * Uout are caller-owned device arrays in the box layout (NV components);
+ * Uout receives U(dt) and may be U itself.  At most 32 species.
+ * Stream-ordered on the handle's stream; a cell whose temperature solve
+ * fails or whose step size collapses sets the device status reported by
+ * the next synchronising call (SMC_ERR_NONCONVERGED).  SMC_ERR_ARG for bad
+ * arguments or host pointers. */
+smc_status smc_react_integrate(smc_handle *h, const double *U, const double *G, double dt,
+                               double *Uout);
 
 /* Message describing the last error on this handle ("" if none).  The
  * string is owned by the handle. */

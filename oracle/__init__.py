@@ -21,7 +21,12 @@ Plain, slow, FP64 NumPy restatement of what the paper's method computes:
                    and Sec. 2.4).
 * ``sdc``       -- Gauss-Lobatto collocation, the Q and S integration
                    matrices, the SDC sweep (Sec. 3.1, eq. expsdc) and the
-                   mode-1 multirate sweep (Sec. 3.2, eq. mrupdate).
+                   mode-1 and mode-2 multirate sweeps (Sec. 3.2, eqs.
+                   mrupdate and mrupdate2).
+* ``bdf``       -- a variable-order, variable-step BDF integrator (the
+                   implicit reaction integration of mode 2).
+* ``react``     -- the reaction ODE of one cell with constant forcing, its
+                   analytic Jacobian, and its integration by ``bdf``.
 * ``heat2d``    -- the appendix heat-equation problems T1/T2 (App. A).
 
 Where the paper is silent the readings are stated in each function and

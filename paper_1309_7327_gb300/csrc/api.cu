@@ -2,6 +2,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cfloat>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -29,6 +30,9 @@ struct smc_handle {
   int rates32 = 0;                      // FP32-mantissa production rates (mixed only)
   int fine_repeat = 1;                  // groups of fine nodes per coarse interval (type (c) if > 1)
   double sdc_exit = 0.0;                // residual early exit threshold (0: off)
+  int mr_mode = 1;                      // multirate mode: 1 explicit, 2 implicit reactions
+  double bdf_rtol = 1e-8, bdf_atol = 1e-12;
+  unsigned long long *d_bdfcnt = nullptr;   // BDF counters (kernels_bdf.cu)
   int x_outflow = 0;                    // non-periodic x ends
   int nx_domain = 0;
   std::vector<BcCell> hbc;              // cells next to the x ends
@@ -630,6 +634,211 @@ smc_status sdc_multirate(smc_handle *h, double *U, const void *key, double dt, i
   return SMC_OK;
 }
 
+// BDF settings of the handle for one interval of length dtp.
+BdfParams bdf_params(smc_handle *h, const double *U, const double *G, double dtp, double *Rbar,
+                     double *Uout) {
+  BdfParams P;
+  memset(&P, 0, sizeof(P));
+  P.U = U;
+  P.G = G;
+  P.Rbar = Rbar;
+  P.Uout = Uout;
+  P.counters = h->d_bdfcnt;
+  P.dtp = dtp;
+  P.rtol = h->bdf_rtol;
+  P.atol = h->bdf_atol;
+  P.eta = std::max(10.0 * DBL_EPSILON / P.rtol, std::min(0.03, std::sqrt(P.rtol)));
+  P.gam[0] = 0.0;
+  for (int k = 1; k < 6; ++k) P.gam[k] = P.gam[k - 1] + 1.0 / k;
+  P.max_attempts = 20000;
+  return P;
+}
+
+smc_status ensure_bdf(smc_handle *h) {
+  if (h->ns > bdf_species_limit())
+    return fail(h, SMC_ERR_ARG, "implicit reactions support at most 32 species");
+  if (!h->d_bdfcnt) {
+    CUDA_TRY(h, dalloc(h, &h->d_bdfcnt, 5));
+    CUDA_TRY(h, cudaMemsetAsync(h->d_bdfcnt, 0, 5 * sizeof(unsigned long long), h->stream));
+  }
+  return SMC_OK;
+}
+
+// MRSDC mode 2 (eq. mrupdate2): the reactions are the coarse component,
+// held at the right node p + 1 of each coarse interval and implicit;
+// advection-diffusion is the fine component (forward-Euler substeps at the
+// fine nodes).  The implicit term is the mean rate Rt = (y(dt_p) - y(0))/dt_p
+// - G of the interval's reaction ODE dU/dtau = R(U) + G integrated by the
+// BDF method.  Per coarse interval p of a sweep:
+//   G1 = (dt/dt_p) sum_{q in p} [(S21 F1^k)_q + (S22 F2^k)_q] - Rt^k_{p+1};  Rt' from U_p, G1
+//   W_{q+1} = W_q + dt_q (Rt' - Rt^k_{p+1}) + dt_q (A(W_q) - A^k_q) + dt (S22 F2^k + S21 F1^k)_q
+//   G2 = G1 + (1/dt_p) sum_q dt_q (A(W_q) - A^k_q);  U^{k+1}_{p+1} = y(dt_p) from U_p, G2,
+//        Rt^{k+1}_{p+1} its mean rate
+//   F1^{k+1}_{p+1} = R(U^{k+1}_{p+1})
+// F1 (true R at the coarse nodes) feeds the quadratures; spread start
+// F1^0 = Rt^0 = R(U_0), F2^0 = A(U_0).  At a fixed point the substeps W end
+// at U^{k+1}_{p+1} and U is the multirate collocation solution; the second
+// integration keeps the advection corrections inside the implicit solve of
+// the end value, which a stiff R needs.
+smc_status sdc_multirate2(smc_handle *h, double *U, const void *key, double dt, int coarse,
+                          int sweeps, int fine) {
+  const int repeat = h->fine_repeat;
+  const int M1 = coarse - 1, sub = fine - 1, per = sub * repeat, M2 = M1 * per;
+  if (M1 > 4 || sub > 8 || M2 > 64) return fail(h, SMC_ERR_ARG, "too many multirate nodes");
+  if (per > 10) return fail(h, SMC_ERR_ARG, "mode 2: at most 10 fine intervals per coarse interval");
+  smc_status st = ensure_bdf(h);
+  if (st) return st;
+  std::vector<double> t1, t2, S21, S22;
+  multirate_matrices(coarse, fine, repeat, t1, t2, S21, S22);
+  // advection-diffusion (nv comps): slot t for fine node t (slot 0 the
+  // recycled A(U_0)), updated in place after each coarse interval; `per`
+  // scratch slots for an interval's new values; the forcing G; the substep
+  // state W.  Reactions (ns comps): slot 0 R(U_0); true R at coarse nodes
+  // 1..M1 and the interval means Rt, two sets each (old / new sweep); Rt'.
+  const int sA = M2 + 1, sG = M2 + 1 + per, sW = M2 + 2 + per;
+  st = ensure_pools(h, M2 + 3 + per, 2 + 4 * M1);
+  if (st) return st;
+  const long long N = h->ncells;
+  const long long n = (long long)h->nv * N, nsN = (long long)h->ns * N;
+  const size_t abytes = (size_t)n * sizeof(double);
+  CUDA_TRY(h, cudaMemcpyAsync(h->d_U0, U, abytes, cudaMemcpyDeviceToDevice, h->stream));
+  if (!(h->cache_kind == 2 && h->cache_U == key && h->cache_f == 0 && h->cache_r == 0)) {
+    st = eval_rhs(h, h->d_U0, h->fpool[0], 1, 0);
+    if (st) return st;
+    { Timed t(h, SMC_K_CHEM); launch_chem_only(state(h), h->d_U0, h->rpool[0], h->stream); }
+    h->n_rhs++;
+    h->n_react++;
+  }
+  std::vector<int> F1old(M1 + 1, 0), Rtold(M1 + 1, 0), F1new(M1 + 1, 0), Rtnew(M1 + 1, 0);
+  double *G = h->fpool[sG];
+  double *W = h->fpool[sW];
+  double *Rt1 = h->rpool[1 + 4 * M1];
+  int set = 0;
+  DevState s = state(h);
+  for (int k = 0; k < sweeps; ++k) {
+    for (int p = 1; p <= M1; ++p) {
+      F1new[p] = 1 + set * M1 + p - 1;
+      Rtnew[p] = 1 + 2 * M1 + set * M1 + p - 1;
+    }
+    // the old A at fine node t: A(U_0) everywhere in the first sweep
+    auto A_old = [&](int t) { return h->fpool[k == 0 ? 0 : t]; };
+    for (int p = 0; p < M1; ++p) {
+      const int q0 = p * per;
+      const double dtp = dt * (t1[p + 1] - t1[p]);
+      const double *Up = p == 0 ? h->d_U0 : U;
+      {
+        // G1: the quadrature terms of the interval per unit time, minus Rt^k
+        Timed t(h, SMC_K_UPDATE);
+        Combo ca;
+        memset(&ca, 0, sizeof(ca));
+        for (int node = q0; node <= q0 + per; ++node) {
+          double wsum = 0.0;
+          for (int q = q0; q < q0 + per; ++q) wsum += S22[q * (M2 + 1) + node];
+          if (wsum == 0.0) continue;
+          ca.c[ca.nsrc] = dt / dtp * wsum;
+          ca.src[ca.nsrc++] = A_old(node);
+        }
+        launch_combo(nullptr, G, ca, n, h->stream);
+        Combo cr;
+        memset(&cr, 0, sizeof(cr));
+        for (int j = 0; j <= M1; ++j) {
+          double wsum = 0.0;
+          for (int q = q0; q < q0 + per; ++q) wsum += S21[q * (M1 + 1) + j];
+          cr.c[cr.nsrc] = dt / dtp * wsum;
+          cr.src[cr.nsrc++] = h->rpool[F1old[j]];
+        }
+        cr.c[cr.nsrc] = -1.0;
+        cr.src[cr.nsrc++] = h->rpool[Rtold[p + 1]];
+        launch_combo(G + 5 * N, G + 5 * N, cr, nsN, h->stream);
+      }
+      {
+        const BdfParams P = bdf_params(h, Up, G, dtp, Rt1, nullptr);
+        Timed t(h, SMC_K_BDF);
+        launch_react_bdf(s, P, h->stream);
+      }
+      // the fine substeps (eq. mrupdate2 with f_slow(U^{k+1}_{p+1}) = Rt')
+      for (int q = q0; q < q0 + per; ++q) {
+        const double dtq = dt * (t2[q + 1] - t2[q]);
+        const double *Aq = h->fpool[0];
+        if (q > 0) {
+          st = eval_rhs(h, q == q0 ? Up : W, h->fpool[sA + q - q0], 1, 0);
+          if (st) return st;
+          h->n_rhs++;
+          Aq = h->fpool[sA + q - q0];
+        }
+        Timed t(h, SMC_K_UPDATE);
+        Combo ca;
+        memset(&ca, 0, sizeof(ca));
+        ca.c[ca.nsrc] = dtq;
+        ca.src[ca.nsrc++] = Aq;
+        for (int node = q0; node <= q0 + per; ++node) {
+          const double wq = dt * S22[q * (M2 + 1) + node] - (node == q ? dtq : 0.0);
+          if (wq == 0.0) continue;
+          ca.c[ca.nsrc] = wq;
+          ca.src[ca.nsrc++] = A_old(node);
+        }
+        launch_combo(q == q0 ? Up : W, W, ca, n, h->stream);
+        Combo cr;
+        memset(&cr, 0, sizeof(cr));
+        cr.c[cr.nsrc] = dtq;
+        cr.src[cr.nsrc++] = Rt1;
+        cr.c[cr.nsrc] = -dtq;
+        cr.src[cr.nsrc++] = h->rpool[Rtold[p + 1]];
+        for (int j = 0; j <= M1; ++j) {
+          cr.c[cr.nsrc] = dt * S21[q * (M1 + 1) + j];
+          cr.src[cr.nsrc++] = h->rpool[F1old[j]];
+        }
+        launch_combo(W + 5 * N, W + 5 * N, cr, nsN, h->stream);
+      }
+      {
+        // G2 = G1 + (1/dt_p) sum_q dt_q (A^{k+1}_q - A^k_q)
+        Timed t(h, SMC_K_UPDATE);
+        Combo cn, co;
+        memset(&cn, 0, sizeof(cn));
+        memset(&co, 0, sizeof(co));
+        for (int q = q0; q < q0 + per; ++q) {
+          const double wq = dt * (t2[q + 1] - t2[q]) / dtp;
+          cn.c[cn.nsrc] = wq;
+          cn.src[cn.nsrc++] = q == 0 ? h->fpool[0] : h->fpool[sA + q - q0];
+          co.c[co.nsrc] = -wq;
+          co.src[co.nsrc++] = A_old(q);
+        }
+        launch_combo(G, G, cn, n, h->stream);
+        launch_combo(G, G, co, n, h->stream);
+      }
+      {
+        const BdfParams P = bdf_params(h, Up, G, dtp, h->rpool[Rtnew[p + 1]], U);
+        Timed t(h, SMC_K_BDF);
+        launch_react_bdf(s, P, h->stream);
+      }
+      { Timed t(h, SMC_K_CHEM); launch_chem_only(s, U, h->rpool[F1new[p + 1]], h->stream); }
+      h->n_react++;
+      // the interval's new A values into their node slots (node 0 keeps A(U_0))
+      for (int q = std::max(q0, 1); q < q0 + per; ++q)
+        CUDA_TRY(h, cudaMemcpyAsync(h->fpool[q], h->fpool[sA + q - q0], abytes,
+                                    cudaMemcpyDeviceToDevice, h->stream));
+    }
+    st = eval_rhs(h, U, h->fpool[M2], 1, 0);
+    if (st) return st;
+    h->n_rhs++;
+    F1old = F1new;
+    Rtold = Rtnew;
+    set ^= 1;
+    h->sweeps_done = k + 1;
+  }
+  // keep A(U_M) and R(U_M) in slot 0 for the next step (graph replay as above)
+  CUDA_TRY(h, cudaMemcpyAsync(h->fpool[0], h->fpool[M2], abytes, cudaMemcpyDeviceToDevice,
+                              h->stream));
+  CUDA_TRY(h, cudaMemcpyAsync(h->rpool[0], h->rpool[F1old[M1]], (size_t)nsN * sizeof(double),
+                              cudaMemcpyDeviceToDevice, h->stream));
+  CUDA_TRY(h, cudaGetLastError());
+  h->cache_kind = 2;
+  h->cache_U = (const double *)key;
+  h->cache_f = 0;
+  h->cache_r = 0;
+  return SMC_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -878,8 +1087,9 @@ smc_status step_body(smc_handle *h, double *Ud, const void *key, double dt, int 
                      int rsub) {
   h->sweeps_done = 0;
   for (double &r : h->resid) r = 0.0;
-  return rsub <= 1 ? sdc_single_rate(h, Ud, key, dt, nodes, sweeps)
-                   : sdc_multirate(h, Ud, key, dt, nodes, sweeps, rsub);
+  if (rsub <= 1) return sdc_single_rate(h, Ud, key, dt, nodes, sweeps);
+  return h->mr_mode == 2 ? sdc_multirate2(h, Ud, key, dt, nodes, sweeps, rsub)
+                         : sdc_multirate(h, Ud, key, dt, nodes, sweeps, rsub);
 }
 
 void drop_graph(smc_handle *h) {
@@ -1073,6 +1283,18 @@ smc_status smc_set_option(smc_handle *h, int key, double v) {
       if (v != 0.0 && v != 1.0) return fail(h, SMC_ERR_ARG, "rates must be 0 or 1");
       h->rates32 = (int)v;
       return SMC_OK;
+    case SMC_OPT_MR_MODE:
+      if (v != 1.0 && v != 2.0) return fail(h, SMC_ERR_ARG, "multirate mode must be 1 or 2");
+      h->mr_mode = (int)v;
+      return SMC_OK;
+    case SMC_OPT_BDF_RTOL:
+      if (!(v > 0.0 && v < 1.0)) return fail(h, SMC_ERR_ARG, "bdf rtol must be in (0, 1)");
+      h->bdf_rtol = v;
+      return SMC_OK;
+    case SMC_OPT_BDF_ATOL:
+      if (!(v >= 0.0) || !std::isfinite(v)) return fail(h, SMC_ERR_ARG, "bdf atol must be >= 0");
+      h->bdf_atol = v;
+      return SMC_OK;
     case SMC_OPT_PROFILE:
       cudaStreamSynchronize(h->stream);
       collect_times(h);
@@ -1108,6 +1330,16 @@ smc_status smc_get_stats(smc_handle *h, smc_stats *o) {
   }
   o->sweeps_done = h->sweeps_done;
   for (int k = 0; k < 64; ++k) o->residual[k] = h->sdc_exit > 0.0 ? h->resid[k] : 0.0;
+  unsigned long long c[5] = {0, 0, 0, 0, 0};
+  if (h->d_bdfcnt) {
+    CUDA_TRY(h, cudaMemcpyAsync(c, h->d_bdfcnt, sizeof(c), cudaMemcpyDeviceToHost, h->stream));
+    CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  }
+  o->bdf_steps = (long long)c[0];
+  o->bdf_rejected = (long long)c[1];
+  o->bdf_newton_failures = (long long)c[2];
+  o->bdf_evals = (long long)c[3];
+  o->bdf_max_steps = (long long)c[4];
   return SMC_OK;
 }
 
@@ -1211,6 +1443,24 @@ smc_status smc_multirate_collocation(int coarse, int fine, int repeat, double *t
   std::copy(b.begin(), b.end(), t2);
   std::copy(c.begin(), c.end(), S21);
   std::copy(d.begin(), d.end(), S22);
+  return SMC_OK;
+}
+
+smc_status smc_react_integrate(smc_handle *h, const double *U, const double *G, double dt,
+                               double *Uout) {
+  if (!h || !h->d_Q) return SMC_ERR_STATE;
+  if (!U || !Uout) return fail(h, SMC_ERR_ARG, "null pointer");
+  if (!(dt > 0) || !std::isfinite(dt)) return fail(h, SMC_ERR_ARG, "dt must be positive");
+  if (!is_device_ptr(U) || !is_device_ptr(Uout) || (G && !is_device_ptr(G)))
+    return fail(h, SMC_ERR_ARG, "U, G and Uout must be device pointers");
+  smc_status st = ensure_bdf(h);
+  if (st) return st;
+  const BdfParams P = bdf_params(h, U, G, dt, nullptr, Uout);
+  {
+    Timed t(h, SMC_K_BDF);
+    launch_react_bdf(state(h), P, h->stream);
+  }
+  CUDA_TRY(h, cudaGetLastError());
   return SMC_OK;
 }
 

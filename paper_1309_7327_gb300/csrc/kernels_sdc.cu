@@ -22,7 +22,7 @@ __global__ void __launch_bounds__(256) k_combo(const double *in, double *out, co
                                                long long n) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x) {
-    double acc = in[i];
+    double acc = in ? in[i] : 0.0;
     for (int j = 0; j < cb.nsrc; ++j) acc += cb.c[j] * cb.src[j][i];
     out[i] = acc;
   }

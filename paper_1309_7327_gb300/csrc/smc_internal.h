@@ -202,7 +202,7 @@ void launch_march_m2(const DevState &s, int dir, float *dUf, int first, int vari
 void launch_final_m(const DevState &s, const double *U, const float *dUf, double *dU, int transport,
                     int chemistry, cudaStream_t st);
 
-// out = in + sum_i c[i] * src[i] over n doubles (n = nv * ncells)
+// out = in + sum_i c[i] * src[i] over n doubles (in may be null: zero)
 struct Combo {
   int nsrc;
   double c[12];
@@ -230,6 +230,24 @@ void launch_fine_chain(const DevState &s, const double *U0, double *U, const Fin
                        cudaStream_t st);
 void launch_chem_only(const DevState &s, const double *U, double *F2, cudaStream_t st);
 void launch_exp(const Mech *m, const double *x, double *y, long long n, cudaStream_t st);
+
+// Implicit reaction integration over one coarse interval (MRSDC mode 2,
+// kernels_bdf.cu): per cell, dU/dtau = R(U) + G on [0, dtp] by the BDF
+// method.  Rbar (ns comps, nullable) receives (y(dtp) - y(0)) / dtp - G_Y,
+// Uout (nv comps, nullable) the state at dtp.
+struct BdfParams {
+  const double *U;                // [nv][ncells] state at tau = 0
+  const double *G;                // [nv][ncells] constant forcing, or null (zero)
+  double *Rbar;
+  double *Uout;
+  unsigned long long *counters;   // [5]: steps, rejected, Newton failures, evaluations,
+                                  //   max steps of a cell (nullable)
+  double dtp, rtol, atol, eta;    // interval, tolerances, Newton tolerance
+  double gam[6];                  // gamma_k = sum_{j<=k} 1/j
+  int max_attempts;
+};
+int bdf_species_limit();
+void launch_react_bdf(const DevState &s, const BdfParams &P, cudaStream_t st);
 
 // Weights and sources of the collocation residual (device-resident table).
 constexpr int SMC_RES_MAX = 80;

@@ -28,13 +28,13 @@ STATUS_NAMES = {0: "SMC_OK", 1: "SMC_ERR_ARG", 2: "SMC_ERR_CUDA", 3: "SMC_ERR_OO
 OPT = dict(precision=0, m47=1, m48=2, diffusion_mode=3, ref_species=4, xi_ratio=5,
            newton_tol=6, newton_maxit=7, t_guess=8, reactions=9, segment=10, profile=11,
            use_graphs=12, x_layout=13, march=14, rates=15,
-           fine_repeat=16, sdc_exit=17, chain_blocks=18)
-KERNELS = ["prim", "grad", "march", "final", "update", "fine", "chem", "other"]
+           fine_repeat=16, sdc_exit=17, chain_blocks=18, mr_mode=19, bdf_rtol=20, bdf_atol=21)
+KERNELS = ["prim", "grad", "march", "final", "update", "fine", "chem", "other", "bdf"]
 
 EXPORTS = ["smc_create", "smc_destroy", "smc_rhs", "smc_sdc_step", "smc_prim_to_cons", "smc_autotune",
            "smc_set_stream", "smc_set_option", "smc_get_stats", "smc_synchronize",
            "smc_invalidate", "smc_collocation", "smc_multirate_collocation", "smc_rhs_noalloc",
-           "smc_exp", "smc_heat2d", "smc_last_error"]
+           "smc_exp", "smc_heat2d", "smc_react_integrate", "smc_last_error"]
 
 
 class smc_grid(C.Structure):
@@ -62,9 +62,11 @@ class smc_bc(C.Structure):
 class smc_stats(C.Structure):
     _fields_ = [("n_rhs", C.c_longlong), ("n_react", C.c_longlong), ("n_steps", C.c_longlong),
                 ("device_flags", C.c_uint), ("nvars", C.c_int), ("ncells", C.c_longlong),
-                ("device_bytes", C.c_longlong), ("launches", C.c_longlong * 8),
-                ("kernel_ms", C.c_double * 8), ("sweeps_done", C.c_int),
-                ("residual", C.c_double * 64)]
+                ("device_bytes", C.c_longlong), ("launches", C.c_longlong * 9),
+                ("kernel_ms", C.c_double * 9), ("sweeps_done", C.c_int),
+                ("residual", C.c_double * 64), ("bdf_steps", C.c_longlong),
+                ("bdf_rejected", C.c_longlong), ("bdf_newton_failures", C.c_longlong),
+                ("bdf_evals", C.c_longlong), ("bdf_max_steps", C.c_longlong)]
 
 
 def load_library(path: str = LIB_PATH) -> C.CDLL:
@@ -90,6 +92,7 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
     lib.smc_heat2d.argtypes = [C.c_int, dp, vp, vp, vp, dp, dp, dp, dp, C.c_int, C.c_int, C.c_int,
                                vp, C.POINTER(C.c_longlong), vp]
     lib.smc_exp.argtypes = [vp, vp, C.c_longlong]
+    lib.smc_react_integrate.argtypes = [vp, vp, vp, dp, vp]
     lib.smc_exp.restype = C.c_int
     lib.smc_rhs_noalloc.argtypes = [C.POINTER(C.c_int), C.POINTER(C.c_double),
                                     C.POINTER(smc_mechanism), vp, vp, vp]
@@ -319,6 +322,14 @@ class Smc:
         self._check(lib().smc_sdc_step(self.h, self._state(U), float(dt), nodes, sweeps,
                                        reaction_substeps))
         return U
+
+    def react_integrate(self, U, G, dt, out):
+        """out = U(dt) of dU/dtau = R(U) + G per cell (implicit BDF; G may be
+        None).  Device tensors of the state's shape; out may be U."""
+        self._check(lib().smc_react_integrate(self.h, self._state(U),
+                                              self._state(G) if G is not None else None,
+                                              float(dt), self._state(out)))
+        return out
 
     def prim_to_cons(self, prim, out):
         self._check(lib().smc_prim_to_cons(self.h, self._state(prim), self._state(out)))
