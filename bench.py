@@ -54,6 +54,9 @@ def parse():
                     help="multirate fine-node groups per coarse interval (1: type (b), >1: type (c))")
     ap.add_argument("--sdc-exit", type=float, default=0.0,
                     help="residual early-exit threshold (0: every sweep runs)")
+    ap.add_argument("--mr-mode", type=int, default=1, choices=(1, 2),
+                    help="multirate mode: 1 explicit reactions on the fine nodes, 2 implicit "
+                         "reactions (BDF) on the coarse nodes, advection-diffusion on the fine")
     return ap.parse_args()
 
 
@@ -251,6 +254,20 @@ def bench_config(wl, args, main_key, world):
     M1 = nodes - 1
     per = rsub - 1 if rsub >= 2 else 0
     ncells, nv = wl.grid.ncells, 5 + wl.mech.ns
+    if per and args.mr_mode == 2:
+        M2 = M1 * per * max(args.fine_repeat, 1)
+        return {"workload": args.workload + (f" (n={args.n})" if args.n else ""),
+                "boxes": wl.grid.nboxes, "cells": ncells,
+                "species": wl.mech.ns, "reactions": wl.mech.nr,
+                "boundaries": "x outflow, y z periodic" if wl.x_outflow else "periodic",
+                "integrator": (f"MRSDC mode 2: reactions implicit (BDF, rtol 1e-8) on {nodes} coarse "
+                               f"GL nodes, advection-diffusion on {rsub} fine GL nodes per coarse "
+                               f"interval, {sweeps} sweeps"),
+                "rhs_evals_per_step": sweeps * M2,
+                "reaction_evals_per_step": "adaptive (bdf_evals in the stats)",
+                "precision": PRECISION_TEXT[main_key],
+                "l2": "inputs larger than L2 (state %.0f MB)" % (nv * ncells * 8 / 1e6),
+                "parallelism": "replicas" if world > 1 else "single GPU"}
     return {"workload": args.workload + (f" (n={args.n})" if args.n else ""),
             "boxes": wl.grid.nboxes, "cells": ncells,
             "species": wl.mech.ns, "reactions": wl.mech.nr,
@@ -331,6 +348,14 @@ def run_heat(args):
     per_step = 8 * arrays * 8 + 8 * 7 * 8      # evaluations + node updates (5 F sources, U in, U out)
     bytes_ = N * N * per_step * args.steps
     peak = measured_peaks().get("hbm_gbs", 6800.0)
+    # FP64 work of one evaluation per cell, each face counted once: a face is
+    # 7 differences, 44 + 8 FMAs (the banded 8 x 8 narrow matrix), and a cell
+    # takes two faces (x, y), two face differences, one sum (+ the source)
+    face = 7 + 2 * (44 + 8)
+    flops_eval = N * N * (2 * face + 3 + (2 if G is not None else 0))
+    sm_mhz = clocks.get("sm_mhz") or 2070.0
+    fp64_peak = SM_COUNT * 4 * sm_mhz * 1e6
+    fl_s = flops_eval * evals / (ms / 1e3)
     line = {"metric": f"Mcell-RHS/s (heat {args.workload.upper()})", "value": value,
             "unit": "Mcell-RHS/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -338,9 +363,14 @@ def run_heat(args):
             "config": {"workload": args.workload, "grid": f"{N}x{N} periodic",
                        "integrator": "SDC 3 GL, 4 sweeps", "stencil": "8th-order narrow (SMC)",
                        "l2": "state and coefficients larger than L2 (%.0f MB)" % (N * N * 8 * 5 / 1e6)},
-            "roofline": {"bound": "hbm", "kernel": "whole step (k_heat_rhs + k_combo)",
-                         "achieved": bytes_ / (ms / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
-                         "frac": bytes_ / (ms / 1e3) / 1e9 / peak, "traffic": None},
+            "roofline": {"bound": "alu", "kernel": "whole step (k_heat_rhs + k_combo), FP64 flops of "
+                                                    "the evaluations",
+                         "achieved": fl_s / 1e12, "peak": fp64_peak / 1e12, "unit": "TFLOP/s",
+                         "frac": fl_s / fp64_peak, "traffic": None,
+                         "peak_source": "FP64 pipe: 152 SMs x 2 FMA/clk x median SM clock under load"},
+            "hbm": {"kernel": "whole step", "algorithmic_bytes_per_step": N * N * per_step,
+                    "achieved_gbs": bytes_ / (ms / 1e3) / 1e9, "peak_gbs": peak,
+                    "frac": bytes_ / (ms / 1e3) / 1e9 / peak},
             "clocks": clocks, "gpu_launches": int(2 * evals)}
     print(json.dumps(line))
 
@@ -367,6 +397,8 @@ def main():
     nodes, sweeps, rsub = wl.nodes, wl.sweeps, wl.reaction_substeps
     M1 = nodes - 1
     evals_per_step = sweeps * M1
+    if args.mr_mode == 2 and rsub >= 2:
+        evals_per_step = sweeps * M1 * (rsub - 1) * max(args.fine_repeat, 1)
     ncells = wl.grid.ncells
     nv = 5 + wl.mech.ns
 
@@ -377,6 +409,8 @@ def main():
             v["fine_repeat"] = args.fine_repeat
         if args.sdc_exit > 0:
             v["sdc_exit"] = args.sdc_exit
+        if args.mr_mode == 2:
+            v["mr_mode"] = 2
 
     def measure(name: str):
         """Warm up, then time args.steps steps on device-resident state."""
@@ -442,6 +476,7 @@ def main():
         st = h.stats()
         launches = {k: st["launches"][k] - base["launches"][k] for k in st["launches"]}
         evals_done = (st["n_rhs"] - base["n_rhs"]) / args.steps      # RHS evaluations per step
+        bdf_evals = st["bdf_evals"] - base["bdf_evals"]
         # the same steps again with every launch timed by CUDA events (eager
         # launches): per-kernel durations for the rooflines
         h.set_option("profile", 1)
@@ -465,7 +500,8 @@ def main():
         ms_eager = e0.elapsed_time(e1) / args.steps
         h.close()
         return dict(ms_step=ms / args.steps, launches=launches, kms=st2["kernel_ms"],
-                    clocks=clocks, U0=U0, tuned=tuned, ms_eager=ms_eager, evals=evals_done)
+                    clocks=clocks, U0=U0, tuned=tuned, ms_eager=ms_eager, evals=evals_done,
+                    bdf_evals=bdf_evals)
 
     runs = {}
     order = {"both": ["mixed", "fp64", "mixed_rates32"]}.get(args.precision, [args.precision])
@@ -529,13 +565,25 @@ def main():
             "traffic": traffic_db.get(f"k_fine_chain:{main_key}:{args.workload}"),
             "peak_source": "FP64 pipe: 152 SMs x 2 FMA/clk x median SM clock under load",
             "share": kms["fine"] / max(sum(kms.values()), 1e-9)}
+    if launches.get("bdf"):
+        bdf_ms = kms["bdf"] / launches["bdf"]
+        evals_launch = R["bdf_evals"] / launches["bdf"]
+        fl = chem_flops_per_eval(wl.mech.ns, wl.mech.nr) * evals_launch
+        rooflines["k_react_bdf"] = {
+            "bound": "alu", "kernel": "k_react_bdf (implicit reactions over one coarse interval)",
+            "achieved": fl / (bdf_ms / 1e3) / 1e12, "peak": fp64_peak / 1e12, "unit": "TFLOP/s",
+            "frac": fl / (bdf_ms / 1e3) / fp64_peak, "traffic": None,
+            "note": "production-rate flops of the counted evaluations only (Jacobian, LU and "
+                    "temperature solves not counted): a lower bound",
+            "peak_source": "FP64 pipe: 152 SMs x 2 FMA/clk x median SM clock under load",
+            "share": kms["bdf"] / max(sum(kms.values()), 1e-9)}
     roofline = max(rooflines.values(), key=lambda r: r["share"]) if rooflines else None
     # HBM-bound stage: SDC / fine-node updates
     peaks = measured_peaks()
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
     per = rsub - 1 if rsub >= 2 else 0
     M1 = nodes - 1
-    if per:
+    if per and launches["fine"]:
         bytes_fine = ncells * 8 * (2 * nv + per * (M1 + 3) * nv + per * (rsub + 2) * wl.mech.ns)
         fine_ms = kms["fine"] / max(launches["fine"], 1)
         hbm = {"kernel": "k_fine_chain", "achieved_gbs": bytes_fine / (fine_ms / 1e3) / 1e9,

@@ -17,59 +17,84 @@ struct HeatParams {
   double M[8][8];                 // narrow-stencil matrix scaled by 1/h^2
 };
 
-// H at the faces left (window offset 0) and right (offset 1) of the middle
-// cell of a 9-cell window, difference-first: H = sum_m a_m sum_{n != 3}
-// M_mn (u_n - u_3), exact since every row of M sums to zero.
-__device__ __forceinline__ double face_diff(const HeatParams &P, const double *a, const double *u) {
-  double H[2];
+// H at the face between window cells 3 and 4 of an 8-cell window (cells
+// c-4 .. c+3 for the face left of cell c), difference-first:
+//   H = sum_m a_m sum_{n != 3} M_mn (u_n - u_3),
+// exact since every row of M sums to zero; M is banded (|m - n| <= 4).
+__device__ __forceinline__ double face_h(const HeatParams &P, const double *a, int as,
+                                         const double *u, int us) {
+  double du[8];
 #pragma unroll
-  for (int o = 0; o < 2; ++o) {
-    double acc = 0.0;
+  for (int n = 0; n < 8; ++n) du[n] = u[n * us] - u[3 * us];
+  double acc = 0.0;
 #pragma unroll
-    for (int m = 0; m < 8; ++m) {
-      double w = 0.0;
+  for (int m = 0; m < 8; ++m) {
+    double w = 0.0;
 #pragma unroll
-      for (int n = 0; n < 8; ++n)
-        if (n != 3 && m - n <= 4 && n - m <= 4) w = fma(P.M[m][n], u[o + n] - u[o + 3], w);
-      acc = fma(a[o + m], w, acc);
-    }
-    H[o] = acc;
+    for (int n = 0; n < 8; ++n)
+      if (n != 3 && m - n <= 4 && n - m <= 4) w = fma(P.M[m][n], du[n], w);
+    acc = fma(a[m * as], w, acc);
   }
-  return H[1] - H[0];
+  return acc;
 }
 
-// F = (a u_x)_x + (b u_y)_y + gs G, one thread per cell, periodic windows
+// F = (a u_x)_x + (b u_y)_y + gs G on a periodic N x N grid.  A block owns
+// a 32 x 16 tile: u, a and b with their 4-cell halos are staged in shared
+// memory, every face of the tile is computed once (33 x 16 x-faces,
+// 32 x 17 y-faces) and each cell takes the difference of its two faces per
+// direction, so the FP64 work per cell is about two faces instead of four.
+constexpr int HTX = 32, HTY = 16;
+
 __global__ void __launch_bounds__(256) k_heat_rhs(int N, const HeatParams P,
                                                   const double *__restrict__ a,
                                                   const double *__restrict__ b,
                                                   const double *__restrict__ G, double gs,
                                                   const double *__restrict__ u,
                                                   double *__restrict__ F) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int j = blockIdx.y * blockDim.y + threadIdx.y;
-  if (i >= N || j >= N) return;
-  double wa[9], wu[9];
-  const size_t row = (size_t)j * N;
-#pragma unroll
-  for (int k = 0; k < 9; ++k) {
-    int ii = i + k - 4;
-    ii += ii < 0 ? N : 0;
-    ii -= ii >= N ? N : 0;
-    wa[k] = __ldg(a + row + ii);
-    wu[k] = __ldg(u + row + ii);
+  __shared__ double su[HTY + 8][HTX + 8];
+  __shared__ double sa[HTY][HTX + 8];
+  __shared__ double sb[HTY + 8][HTX];
+  __shared__ double hx[HTY][HTX + 1];
+  __shared__ double hy[HTY + 1][HTX];
+  const int x0 = blockIdx.x * HTX, y0 = blockIdx.y * HTY;
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+  const int nt = blockDim.x * blockDim.y;
+  auto wrap = [N](int i) {
+    i %= N;
+    return i < 0 ? i + N : i;
+  };
+  for (int idx = tid; idx < (HTY + 8) * (HTX + 8); idx += nt) {
+    const int r = idx / (HTX + 8), c = idx % (HTX + 8);
+    su[r][c] = __ldg(u + (size_t)wrap(y0 + r - 4) * N + wrap(x0 + c - 4));
   }
-  double f = face_diff(P, wa, wu);
-#pragma unroll
-  for (int k = 0; k < 9; ++k) {
-    int jj = j + k - 4;
-    jj += jj < 0 ? N : 0;
-    jj -= jj >= N ? N : 0;
-    wa[k] = __ldg(b + (size_t)jj * N + i);
-    wu[k] = __ldg(u + (size_t)jj * N + i);
+  for (int idx = tid; idx < HTY * (HTX + 8); idx += nt) {
+    const int r = idx / (HTX + 8), c = idx % (HTX + 8);
+    sa[r][c] = __ldg(a + (size_t)wrap(y0 + r) * N + wrap(x0 + c - 4));
   }
-  f += face_diff(P, wa, wu);
-  if (G) f = fma(gs, __ldg(G + row + i), f);
-  F[row + i] = f;
+  for (int idx = tid; idx < (HTY + 8) * HTX; idx += nt) {
+    const int r = idx / HTX, c = idx % HTX;
+    sb[r][c] = __ldg(b + (size_t)wrap(y0 + r - 4) * N + wrap(x0 + c));
+  }
+  __syncthreads();
+  for (int idx = tid; idx < HTY * (HTX + 1); idx += nt) {
+    const int r = idx / (HTX + 1), f = idx % (HTX + 1);
+    hx[r][f] = face_h(P, &sa[r][f], 1, &su[r + 4][f], 1);
+  }
+  for (int idx = tid; idx < (HTY + 1) * HTX; idx += nt) {
+    const int f = idx / HTX, c = idx % HTX;
+    hy[f][c] = face_h(P, &sb[f][c], HTX, &su[f][c + 4], HTX + 8);
+  }
+  __syncthreads();
+  for (int idx = tid; idx < HTY * HTX; idx += nt) {
+    const int r = idx / HTX, c = idx % HTX;
+    const int gx = x0 + c, gy = y0 + r;
+    if (gx >= N || gy >= N) continue;
+    const size_t o = (size_t)gy * N + gx;
+    double f = hx[r][c + 1] - hx[r][c];
+    f += hy[r + 1][c] - hy[r][c];
+    if (G) f = fma(gs, __ldg(G + o), f);
+    F[o] = f;
+  }
 }
 
 }  // namespace smc
@@ -116,7 +141,7 @@ extern "C" smc_status smc_heat2d(int N, double h, const double *a, const double 
   }
   double *U0 = buf;
   auto Fp = [&](int k) { return buf + (size_t)(1 + k) * n; };   // k = 0 .. 2M
-  const dim3 blk(32, 8), grd((N + 31) / 32, (N + 7) / 8);
+  const dim3 blk(32, 8), grd((N + HTX - 1) / HTX, (N + HTY - 1) / HTY);
   long long evals = 0;
   smc_status status = SMC_OK;
   auto rhs = [&](const double *x, double *F, double t) {

@@ -5,7 +5,11 @@ Both sides run the same variable-order BDF algorithm; the CUDA one factors
 its Newton matrix in FP32 (the oracle in FP64), so their Newton iterates
 stop at slightly different points inside the Newton tolerance, which is
 1e-4 of the local error tolerance.  The bar is therefore the integrator's
-own tolerance: per element |y_gpu - y_oracle| <= C (rtol |y| + atol rho)."""
+own tolerance: per element |y_gpu - y_oracle| <= C (rtol |y| + atol rho).
+Measured: C ~ 1e-5 (the two sides take the same step and order decisions,
+and the Newton iterates converge well inside their stopping test); the
+small-grid bars allow 1e-2, the full-size sampled one 10 (one cell whose
+accept/reject decision flipped would differ by about the tolerance)."""
 import numpy as np
 import pytest
 
@@ -61,7 +65,7 @@ def test_react_integrate_matches_oracle_every_cell(smc):
     ref = react.integrate(U, G, dt, wl.mech, rtol=RTOL, atol=ATOL)
     assert np.allclose(got[:5], U[:5] + dt * G[:5], rtol=1e-15, atol=0)
     r = tol_ratio(got[5:], ref[5:], U[0][None])
-    assert r < 10.0, r
+    assert r < 1e-2, r
     # the composition moved by far more than the tolerance
     assert np.abs(ref[5:] - U[5:]).max() > 1e4 * RTOL * np.abs(U[5:]).max()
     assert st["bdf_steps"] >= U.shape[1] and st["bdf_evals"] > st["bdf_steps"]
@@ -78,7 +82,7 @@ def test_react_integrate_in_place_and_without_forcing(smc):
     cells = list(range(0, U.shape[1], 7))
     ref = react.integrate(U, None, dt, wl.mech, rtol=RTOL, atol=ATOL, cells=cells)
     assert np.array_equal(got[:5], U[:5])
-    assert tol_ratio(got[5:, cells], ref[5:], U[0][None, cells]) < 10.0
+    assert tol_ratio(got[5:, cells], ref[5:], U[0][None, cells]) < 1e-2
     # mass: sum_k rho Y_k = rho at every cell
     assert np.abs(got[5:].sum(0) - got[0]).max() <= 1e-12 * got[0].max()
 
@@ -134,7 +138,7 @@ def test_mode2_step_matches_oracle(smc, fine, sweeps):
     ref = synth.global_to_boxes(wl.grid, ref)
     M2 = 2 * (fine - 1)
     assert (st["n_rhs"], st["n_react"]) == (nA, nR) == (sweeps * M2 + 1, sweeps * 2 + 1)
-    assert tol_ratio(got[5:], ref[5:], U[0][None]) < 50.0
+    assert tol_ratio(got[5:], ref[5:], U[0][None]) < 1e-2
     err = relerr(got[:5] - U[:5], ref[:5] - U[:5])
     assert err.max() < 1e-7, err
 
