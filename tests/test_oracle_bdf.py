@@ -196,3 +196,44 @@ def test_reaction_ode_with_forcing_moves_the_linear_components():
     out, _ = react.integrate_cell(U, G, dt, m)
     assert np.allclose(out[:5], U[:5] + dt * G[:5], rtol=1e-15, atol=0)
     assert abs(out[5:].sum() - out[0]) <= 1e-12 * out[0]
+
+
+def test_mode2_fixed_point_on_a_chemistry_cell_is_lobatto_collocation():
+    """With no advection-diffusion, the mode-2 sweeps (BDF integration of the
+    reactions over each coarse interval) converge to the 3-node Lobatto IIIA
+    collocation solution of the cell's reaction ODE, solved independently as
+    one nonlinear system."""
+    import scipy.optimize as so
+    from oracle import sdc
+    m = synth.make_mechanism(3, 2, 1, kmax=1e9)
+    rng = np.random.default_rng(8)
+    Y = rng.uniform(0.1, 1.0, 3)
+    Y /= Y.sum()
+    prim = np.concatenate([[100.0, 0.0, -50.0, 1450.0, thermo.P_ATM], Y]).reshape(-1, 1)
+    u0 = thermo.conserved(prim, m.nasa7, m.W)[:, 0]
+    f, jac, y0, rho0 = react.cell_ode(u0, np.zeros(8), m)
+    dt = 2e-8
+
+    def fR(u):
+        fu, _, yu, _ = react.cell_ode(u, np.zeros(8), m)
+        out = np.zeros(8)
+        out[5:] = fu(0.0, yu)
+        return out
+
+    integ = lambda Up, G, dtp: react.integrate_cell(Up, G, dtp, m, rtol=1e-12,   # noqa: E731
+                                                    atol=1e-18)[0]
+    u2 = sdc.mrsdc2_step(u0, lambda u: np.zeros(8), fR, integ, dt, coarse=3, fine=3, sweeps=30,
+                         species=slice(5, 8))[0]
+    tau = sdc.gauss_lobatto(3)
+    Q = sdc.q_matrix(tau)
+
+    def resid(x):
+        Yn = x.reshape(2, 3)
+        F = [f(0.0, y0)] + [f(tau[k + 1] * dt, Yn[k]) for k in range(2)]
+        return np.concatenate([Yn[k] - y0 - dt * sum(Q[k, j] * F[j] for j in range(3))
+                               for k in range(2)]) / rho0
+
+    yc = so.fsolve(resid, np.concatenate([y0, y0]), xtol=1e-14).reshape(2, 3)[1]
+    change = np.abs(yc - y0).max()
+    assert change > 1e-4 * rho0                       # the chemistry moved
+    assert np.abs(u2[5:] - yc).max() < 1e-9 * change
