@@ -29,10 +29,17 @@ family it belongs to, written from the textbook form of the BDF methods:
 * Starting step: the algorithm of Hairer, Norsett & Wanner (Solving ODEs I,
   Sec. II.4) for a first-order start.
 
-The Jacobian is re-evaluated at the predicted point of every step attempt
-(no reuse across steps), so the integrator has no Jacobian-age heuristics.
-The constants below (NEWTON_MAXITER, the Newton tolerance, the factors)
-are this restatement's choices; the CUDA integrator uses the same ones.
+* The Newton matrix I - c J (c = h / gamma_k) is kept across steps, as in
+  VODE: it is rebuilt (Jacobian at the predicted point, new factors) when
+  there is none, after 20 steps, when c has moved by more than 30% since
+  the factorisation, or when the Newton iteration failed with an old one
+  (the step is then retried with the same h); with an old matrix the
+  correction is scaled by 2 / (1 + c / c_lu).  A Newton failure with a new
+  matrix halves the step.
+
+The constants (NEWTON_MAXITER, the Newton tolerance, the factors, the
+rebuild thresholds) are this restatement's choices; the CUDA integrator
+uses the same ones.
 """
 from __future__ import annotations
 
@@ -46,6 +53,8 @@ NEWTON_MAXITER = 4
 SAFETY = 0.9
 MIN_FACTOR = 0.2
 MAX_FACTOR = 10.0
+LU_MAX_STEPS = 20       # steps before the Newton matrix is rebuilt regardless
+LU_MAX_CHANGE = 0.3     # |c / c_lu - 1| above which it is rebuilt
 EPS = float(np.finfo(np.float64).eps)
 
 GAMMA = np.array([0.0] + [sum(1.0 / j for j in range(1, m + 1)) for m in range(1, MAX_ORDER + 1)])
@@ -122,6 +131,7 @@ def bdf_integrate(f, jac, t_end: float, y0: np.ndarray, wabs: np.ndarray, rtol: 
     n_equal = 0
     t = 0.0
     attempts = 0
+    lu, c_lu, since_lu = None, 1.0, 0
     while t < t_end:
         attempts += 1
         if attempts > max_attempts or h <= 1e-14 * t_end:
@@ -137,10 +147,18 @@ def bdf_integrate(f, jac, t_end: float, y0: np.ndarray, wabs: np.ndarray, rtol: 
         psi = (GAMMA[1:k + 1] @ D[1:k + 1]) / GAMMA[k]
         c = h / GAMMA[k]
         w = wabs + rtol * np.abs(D[0])
-        fy, J = jac(t + h, y_pred)
-        stats["jac_evals"] += 1
+        fresh = lu is None or since_lu >= LU_MAX_STEPS or abs(c / c_lu - 1.0) > LU_MAX_CHANGE
+        if fresh:
+            fy, J = jac(t + h, y_pred)
+            stats["jac_evals"] += 1
+            lu = sla.lu_factor(np.eye(n) - c * J)
+            c_lu = c
+            since_lu = 0
+        else:
+            fy = f(t + h, y_pred)
         stats["f_evals"] += 1
-        lu = sla.lu_factor(np.eye(n) - c * J)
+        # a matrix factored at another c: scale the correction (VODE's rule)
+        scale = 2.0 / (1.0 + c / c_lu)
         d = np.zeros(n)
         y = y_pred.copy()
         converged = False
@@ -149,7 +167,7 @@ def bdf_integrate(f, jac, t_end: float, y0: np.ndarray, wabs: np.ndarray, rtol: 
             if it > 0:
                 fy = f(t + h, y)
                 stats["f_evals"] += 1
-            delta = sla.lu_solve(lu, c * fy - psi - d)
+            delta = scale * sla.lu_solve(lu, c * fy - psi - d)
             y = y + delta
             d = d + delta
             dn = _rms(delta / w)
@@ -166,6 +184,9 @@ def bdf_integrate(f, jac, t_end: float, y0: np.ndarray, wabs: np.ndarray, rtol: 
             dn_old = dn
         if not converged:
             stats["newton_failures"] += 1
+            if not fresh:
+                lu = None                 # retry the step with a new Jacobian
+                continue
             D[:k + 1] = rescale_matrix(k, 0.5) @ D[:k + 1]
             h *= 0.5
             n_equal = 0
@@ -180,6 +201,7 @@ def bdf_integrate(f, jac, t_end: float, y0: np.ndarray, wabs: np.ndarray, rtol: 
             continue
         # accepted: t_{n+1}, and the differences of y_{n+1}
         t = t_end if last else t + h
+        since_lu += 1
         stats["steps"] += 1
         stats["orders"].append(k)
         D[k + 2] = d - D[k + 1]

@@ -251,7 +251,8 @@ def mrsdc_step(U0, f1, f2, dt: float, coarse: int = 3, fine: int = 5, repeat: in
 
 
 def mrsdc2_step(U0, fA, fR, integrate, dt: float, coarse: int = 3, fine: int = 5,
-                repeat: int = 1, sweeps: int = 4, FA0=None, FR0=None, species=None):
+                repeat: int = 1, sweeps: int = 4, FA0=None, FR0=None, species=None,
+                eps: float = 0.0, history=None):
     """One mode-2 MRSDC step (eq. mrupdate2): the reactions R are the coarse
     component (nodes t1), advection-diffusion A the fine one (nodes t2,
     forward-Euler substeps).  Returns (U_new, A(U_new), R(U_new), n_A, n_R).
@@ -285,7 +286,9 @@ def mrsdc2_step(U0, fA, fR, integrate, dt: float, coarse: int = 3, fine: int = 5
 
     fR returns full-size arrays (zero outside the species components);
     `species` is the index (slice or mask) of those components, used to
-    zero Rt outside them."""
+    zero Rt outside them.  eps > 0: the residual of eq. residual (the
+    coarse quadrature of R, the fine one of A) after every sweep goes to
+    `history` and the step ends by stop_rule, as in mrsdc_step."""
     t1, t2, S21, S22 = mr_matrices(coarse, fine, repeat)
     M1, M2 = coarse - 1, t2.shape[0] - 1
     per = M2 // M1
@@ -337,4 +340,12 @@ def mrsdc2_step(U0, fA, fR, integrate, dt: float, coarse: int = 3, fine: int = 5
         F2new[M2] = fA(U)
         nA += 1
         F1old, F2old, Rtold = F1new, F2new, Rtnew
+        if eps > 0.0:
+            q1 = S21.sum(axis=0)
+            q2 = S22.sum(axis=0)
+            R = (U0 + dt * sum(q1[j] * F1old[j] for j in range(M1 + 1))
+                 + dt * sum(q2[t] * F2old[t] for t in range(M2 + 1)) - U)
+            history.append(residual_norm(R, U0))
+            if stop_rule(history, eps):
+                break
     return U, F2old[M2], F1old[M1], nA, nR

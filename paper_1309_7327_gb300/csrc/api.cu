@@ -825,6 +825,30 @@ smc_status sdc_multirate2(smc_handle *h, double *U, const void *key, double dt, 
     Rtold = Rtnew;
     set ^= 1;
     h->sweeps_done = k + 1;
+    if (h->sdc_exit > 0.0) {
+      // eq. residual: the fine quadrature of A (q2_t = sum_q S22_qt), the
+      // coarse one of the reactions (q1_j = sum_q S21_qj); every A slot
+      // holds this sweep's value now
+      ResidualTable tab;
+      memset(&tab, 0, sizeof(tab));
+      tab.n1 = M2 + 1;
+      tab.n2 = M1 + 1;
+      for (int t = 0; t <= M2; ++t) {
+        double q = 0.0;
+        for (int qq = 0; qq < M2; ++qq) q += S22[qq * (M2 + 1) + t];
+        tab.c1[t] = dt * q;
+        tab.src1[t] = h->fpool[t];
+      }
+      for (int j = 0; j <= M1; ++j) {
+        double q = 0.0;
+        for (int qq = 0; qq < M2; ++qq) q += S21[qq * (M1 + 1) + j];
+        tab.c2[j] = dt * q;
+        tab.src2[j] = h->rpool[F1old[j]];
+      }
+      double r;
+      if ((st = sweep_residual(h, h->d_U0, U, tab, r))) return st;
+      if (residual_says_stop(h, k, r)) break;
+    }
   }
   // keep A(U_M) and R(U_M) in slot 0 for the next step (graph replay as above)
   CUDA_TRY(h, cudaMemcpyAsync(h->fpool[0], h->fpool[M2], abytes, cudaMemcpyDeviceToDevice,

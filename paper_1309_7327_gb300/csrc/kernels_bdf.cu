@@ -11,9 +11,13 @@
 //   * order-k BDF  gamma_k d + sum_{m=1}^{k} gamma_m nabla^m y_n = h f(y_pred + d),
 //     y_pred = sum_{m=0}^{k} nabla^m y_n, d = nabla^{k+1} y_{n+1};
 //   * Newton on d with the matrix I - (h/gamma_k) J, J = d(rho omega)/dy at
-//     fixed rho and e, evaluated at y_pred in every step attempt; the
-//     residual, the rates and every state update are FP64, J and its LU
-//     factors FP32 (they only set the convergence rate of the iteration);
+//     fixed rho and e; the residual, the rates and every state update are
+//     FP64, J and its LU factors FP32 (they only set the convergence rate of
+//     the iteration).  The factored matrix is kept across steps and rebuilt
+//     (J at the predicted point) when there is none, after 20 steps, when
+//     c = h/gamma_k has moved by more than 30%, or when the iteration failed
+//     with an old one (the step is then retried with the same h); an old
+//     matrix's corrections are scaled by 2 / (1 + c / c_lu);
 //   * local error d/(k+1) in the RMS norm with weights atol rho_0 + rtol |y_n|;
 //   * step changes resample the interpolating polynomial (quasi-constant
 //     step size); order k-1, k or k+1 chosen after k+1 equal steps by the
@@ -32,6 +36,8 @@ namespace {
 
 constexpr int KMAX = 5;            // highest BDF order
 constexpr int NEWTON_MAXITER = 4;
+constexpr int LU_MAX_STEPS = 20;   // steps before the Newton matrix is rebuilt regardless
+constexpr double LU_MAX_CHANGE = 0.3;
 
 struct CellConst {
   double rho0, m0[3], E0;          // non-species components at tau = 0
@@ -332,8 +338,9 @@ __global__ void __launch_bounds__(128) k_react_bdf(const DevState s, const BdfPa
   const double T_end = P.dtp;
   const double wabs = P.atol * c.rho0;
   double t = 0.0, h = 0.0, h0 = 0.0, ch = 0.0, dn_old = 0.0, d1 = 0.0;
-  int k = 1, n_equal = 0, it = 0, attempts = 0, phase = PH_F0;
-  bool last = false;
+  double c_lu = 1.0, corr = 1.0;
+  int k = 1, n_equal = 0, it = 0, attempts = 0, phase = PH_F0, since_lu = 0;
+  bool last = false, have_lu = false, fresh = false;
   unsigned long long n_steps = 0, n_rej = 0, n_fail = 0, n_eval = 0;
   bool done = flag != 0 || !(T_end > 0.0);
   while (!done) {
@@ -372,7 +379,8 @@ __global__ void __launch_bounds__(128) k_react_bdf(const DevState s, const BdfPa
       }
       ch = h * ig;
       tau = t + h;
-      wantJ = true;
+      fresh = !have_lu || since_lu >= LU_MAX_STEPS || fabs(ch / c_lu - 1.0) > LU_MAX_CHANGE;
+      wantJ = fresh;
       it = 0;
     }
     const bool ok = ode_eval<NS>(s, c, tau, yv, gY, f, wantJ ? J : nullptr);
@@ -411,14 +419,20 @@ __global__ void __launch_bounds__(128) k_react_bdf(const DevState s, const BdfPa
       continue;
     }
     bool conv = false, fail = !ok;
-    if (!fail && phase == PH_ATTEMPT) fail = !lu_factor<NS>(J, piv, ns, trunc_float(ch));
+    if (!fail && phase == PH_ATTEMPT && fresh) {
+      have_lu = lu_factor<NS>(J, piv, ns, trunc_float(ch));
+      fail = !have_lu;
+      c_lu = ch;
+      since_lu = 0;
+    }
+    if (phase == PH_ATTEMPT) corr = 2.0 / (1.0 + ch / c_lu);
     if (!fail) {
-      // Newton correction: (I - ch J) delta = ch f - psi - d
+      // Newton correction: (I - c_lu J) delta = ch f - psi - d
       for (int j = 0; j < ns; ++j) b[j] = trunc_float(fma(ch, f[j], -psi[j]) - d[j]);
       lu_solve<NS>(J, piv, ns, b);
       double acc = 0.0;
       for (int j = 0; j < ns; ++j) {
-        const double dd = float_to_double(b[j]);
+        const double dd = corr * float_to_double(b[j]);
         y[j] += dd;
         d[j] += dd;
         const double x = dd / w[j];
@@ -439,6 +453,13 @@ __global__ void __launch_bounds__(128) k_react_bdf(const DevState s, const BdfPa
       dn_old = dn;
       ++it;
       if (!conv && !fail && it >= NEWTON_MAXITER) fail = true;
+    }
+    if (fail && !fresh) {
+      // an old matrix: retry the step with a new Jacobian
+      ++n_fail;
+      have_lu = false;
+      phase = PH_ATTEMPT;
+      continue;
     }
     if (fail) {
       ++n_fail;
@@ -464,6 +485,7 @@ __global__ void __launch_bounds__(128) k_react_bdf(const DevState s, const BdfPa
     }
     // accepted: the differences of y_{n+1}
     t = last ? T_end : t + h;
+    ++since_lu;
     ++n_steps;
     for (int j = 0; j < ns; ++j) {
       D[k + 2][j] = d[j] - D[k + 1][j];
@@ -527,6 +549,7 @@ void launch_react_bdf(const DevState &s, const BdfParams &P, cudaStream_t st) {
   if (nb == 0) return;
   if (s.ns <= 8) k_react_bdf<8><<<(unsigned)nb, block, 0, st>>>(s, P);
   else if (s.ns <= 16) k_react_bdf<16><<<(unsigned)nb, block, 0, st>>>(s, P);
+  else if (s.ns <= 24) k_react_bdf<24><<<(unsigned)nb, block, 0, st>>>(s, P);
   else k_react_bdf<32><<<(unsigned)nb, block, 0, st>>>(s, P);
 }
 

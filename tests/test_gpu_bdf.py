@@ -108,7 +108,7 @@ def test_react_integrate_full_size_sampled(smc):
     assert np.isfinite(got).all()
 
 
-def _mode2_oracle(wl, U_g, dt, coarse, fine, sweeps):
+def _mode2_oracle(wl, U_g, dt, coarse, fine, sweeps, repeat=1, eps=0.0, history=None):
     ns = wl.mech.ns
 
     def fA(u):
@@ -121,7 +121,7 @@ def _mode2_oracle(wl, U_g, dt, coarse, fine, sweeps):
         return react.integrate(Up, G, dtp, wl.mech, rtol=RTOL, atol=ATOL)
 
     return osdc.mrsdc2_step(U_g, fA, fR, integ, dt, coarse=coarse, fine=fine, sweeps=sweeps,
-                            species=slice(5, 5 + ns))
+                            repeat=repeat, species=slice(5, 5 + ns), eps=eps, history=history)
 
 
 @pytest.mark.parametrize("fine,sweeps", [(3, 2), (2, 3)])
@@ -141,6 +141,44 @@ def test_mode2_step_matches_oracle(smc, fine, sweeps):
     assert tol_ratio(got[5:], ref[5:], U[0][None]) < 1e-2
     err = relerr(got[:5] - U[:5], ref[:5] - U[:5])
     assert err.max() < 1e-7, err
+
+
+def test_mode2_type_c_step_matches_oracle(smc):
+    """Two groups of 3 fine Gauss-Lobatto nodes per coarse interval."""
+    wl, U, U_g = state("c1", seed=6, n=8, p_amp=0.03)
+    with smc.Smc(wl.grid, wl.mech, _opts(mr_mode=2, fine_repeat=2)) as h:
+        Ud = dev(U)
+        h.sdc_step(Ud, wl.dt, nodes=3, sweeps=2, reaction_substeps=3)
+        h.synchronize()
+        st = h.stats()
+        got = Ud.cpu().numpy()
+    ref, _, _, nA, nR = _mode2_oracle(wl, U_g, wl.dt, 3, 3, 2, repeat=2)
+    ref = synth.global_to_boxes(wl.grid, ref)
+    assert (st["n_rhs"], st["n_react"]) == (nA, nR) == (2 * 8 + 1, 2 * 2 + 1)
+    assert tol_ratio(got[5:], ref[5:], U[0][None]) < 1e-2
+    assert relerr(got[:5] - U[:5], ref[:5] - U[:5]).max() < 1e-7
+
+
+def test_mode2_residual_exit_matches_oracle(smc):
+    """The mode-2 residual (coarse quadrature of R, fine quadrature of A)
+    after every sweep, and the stagnation exit, against the oracle."""
+    wl, U, U_g = state("c1", seed=7, n=8, p_amp=0.03)
+    with smc.Smc(wl.grid, wl.mech, _opts(mr_mode=2, sdc_exit=0.05)) as h:
+        Ud = dev(U)
+        h.sdc_step(Ud, wl.dt, nodes=3, sweeps=10, reaction_substeps=3)
+        h.synchronize()
+        st = h.stats()
+        got = Ud.cpu().numpy()
+    hist = []
+    ref, _, _, _, _ = _mode2_oracle(wl, U_g, wl.dt, 3, 3, 10, eps=0.05, history=hist)
+    res = st["residual"]
+    assert len(res) == st["sweeps_done"] < 10
+    assert abs(st["sweeps_done"] - len(hist)) <= 1
+    for g, o in zip(res, hist):
+        if o > 1e-9:
+            assert abs(g - o) <= 1e-3 * o, (res, hist)
+    ref = synth.global_to_boxes(wl.grid, ref)
+    assert tol_ratio(got[5:], ref[5:], U[0][None]) < 10.0
 
 
 def test_mode2_two_steps_graphs_and_eager_agree(smc):

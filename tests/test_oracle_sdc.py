@@ -330,3 +330,19 @@ def test_mrsdc2_with_the_bdf_integrator_matches_exact_integration():
     bd, _, _, _, _ = sdc.mrsdc2_step(np.array([u0]), A, R, integ_bdf, dt, coarse=3, fine=3,
                                      sweeps=4)
     assert abs(bd[0] - ex[0]) < 1e-8 * abs(ex[0]) + 1e-13
+
+
+def test_mrsdc2_residual_vanishes_at_the_collocation_solution_and_exit_stops_there():
+    """Mode 2's residual (coarse quadrature of the reactions, fine quadrature
+    of A) is zero at the multirate collocation solution: the sweeps drive it
+    to rounding, the exit stops at stagnation, and the state is the
+    collocation value.  (Its sweeps contract more slowly than mode 1's, so
+    the stagnation threshold is tighter.)"""
+    a, r, dt, u0 = -1.3, -4.0, 0.3, 1.7
+    hist = []
+    U, _, _, _, _ = sdc.mrsdc2_step(np.array([u0]), lambda u: a * u, lambda u: r * u,
+                                    _linear_exact_integrate(r), dt, coarse=3, fine=3, sweeps=60,
+                                    eps=0.05, history=hist)
+    assert 3 < len(hist) < 60 and hist[-1] < 1e-14
+    assert all(hist[i + 1] < hist[i] for i in range(len(hist) - 3))
+    assert abs(U[0] - _mr2_collocation(u0, a, r, dt, 3, 3)) < 1e-13
