@@ -5,8 +5,10 @@
  * compressible Navier-Stokes equations (Emmett, Zhang & Bell, arXiv
  * 1309.7327, Sec. 2.1, eq. cns) on 3-D boxes of a structured grid with the
  * paper's 8th-order spatial discretisation (Sec. 2.2), and advances it with
- * spectral deferred corrections (Sec. 3.1, eq. expsdc) or mode-1 multirate
- * SDC (Sec. 3.2, eq. mrupdate).  One GPU, one CUDA stream per handle.
+ * spectral deferred corrections (Sec. 3.1, eq. expsdc) or multirate SDC
+ * (Sec. 3.2): mode 1 (eq. mrupdate, explicit reactions on the fine nodes) or
+ * mode 2 (eq. mrupdate2, reactions integrated implicitly on the coarse
+ * nodes).  One GPU, one CUDA stream per handle.
  *
  * Units are CGS throughout (cm, g, s, K, erg); activation energies are in
  * cal/mol.  All functions return an smc_status and never abort.

@@ -163,17 +163,19 @@ def test_mode2_residual_exit_matches_oracle(smc):
     """The mode-2 residual (coarse quadrature of R, fine quadrature of A)
     after every sweep, and the stagnation exit, against the oracle."""
     wl, U, U_g = state("c1", seed=7, n=8, p_amp=0.03)
-    with smc.Smc(wl.grid, wl.mech, _opts(mr_mode=2, sdc_exit=0.05)) as h:
+    with smc.Smc(wl.grid, wl.mech, _opts(mr_mode=2, sdc_exit=0.5)) as h:
         Ud = dev(U)
-        h.sdc_step(Ud, wl.dt, nodes=3, sweeps=10, reaction_substeps=3)
+        h.sdc_step(Ud, wl.dt, nodes=3, sweeps=14, reaction_substeps=3)
         h.synchronize()
         st = h.stats()
         got = Ud.cpu().numpy()
     hist = []
-    ref, _, _, _, _ = _mode2_oracle(wl, U_g, wl.dt, 3, 3, 10, eps=0.05, history=hist)
+    ref, _, _, _, _ = _mode2_oracle(wl, U_g, wl.dt, 3, 3, 14, eps=0.5, history=hist)
     res = st["residual"]
-    assert len(res) == st["sweeps_done"] < 10
-    assert abs(st["sweeps_done"] - len(hist)) <= 1
+    # once the residual is at rounding level the exact sweep of the stop
+    # depends on rounding noise on both sides
+    assert len(res) == st["sweeps_done"] < 14, res
+    assert abs(st["sweeps_done"] - len(hist)) <= 2, (res, hist)
     for g, o in zip(res, hist):
         if o > 1e-9:
             assert abs(g - o) <= 1e-3 * o, (res, hist)
