@@ -356,6 +356,14 @@ def run_heat(args):
     sm_mhz = clocks.get("sm_mhz") or 2070.0
     fp64_peak = SM_COUNT * 4 * sm_mhz * 1e6
     fl_s = flops_eval * evals / (ms / 1e3)
+    # ncu DRAM bytes of one k_heat_rhs launch (a 2048^2 capture scaled by cells)
+    heat_traffic = None
+    try:
+        db = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
+        if "k_heat_rhs:t1" in db:
+            heat_traffic = db["k_heat_rhs:t1"] * (N * N) / (4096 * 4096)
+    except (OSError, ValueError):
+        pass
     line = {"metric": f"Mcell-RHS/s (heat {args.workload.upper()})", "value": value,
             "unit": "Mcell-RHS/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -370,7 +378,8 @@ def run_heat(args):
                          "peak_source": "FP64 pipe: 152 SMs x 2 FMA/clk x median SM clock under load"},
             "hbm": {"kernel": "whole step", "algorithmic_bytes_per_step": N * N * per_step,
                     "achieved_gbs": bytes_ / (ms / 1e3) / 1e9, "peak_gbs": peak,
-                    "frac": bytes_ / (ms / 1e3) / 1e9 / peak},
+                    "frac": bytes_ / (ms / 1e3) / 1e9 / peak,
+                    "k_heat_rhs_dram_bytes_per_launch": heat_traffic},
             "clocks": clocks, "gpu_launches": int(2 * evals)}
     print(json.dumps(line))
 
