@@ -296,11 +296,11 @@ __device__ __forceinline__ double step_factor(double err, int p) {
 
 enum { PH_F0 = 0, PH_F1, PH_ATTEMPT, PH_NEWTON };
 
+// One cell: integrate, write its outputs, add its counters to cnt[4] and
+// its accepted steps to the running maximum mx.
 template <int NS>
-__global__ void __launch_bounds__(128) k_react_bdf(const DevState s, const BdfParams P) {
-  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const unsigned lanes = __ballot_sync(0xffffffffu, i < s.ncells);
-  if (i >= s.ncells) return;
+__device__ __forceinline__ void bdf_cell(const DevState &s, const BdfParams &P, long long i,
+                                         unsigned *cnt, unsigned &mx) {
   const long long N = s.ncells;
   const int ns = s.ns;
   unsigned flag = 0;
@@ -323,6 +323,7 @@ __global__ void __launch_bounds__(128) k_react_bdf(const DevState s, const BdfPa
   for (int k = 0; k < ns; ++k) {
     D[0][k] = P.U[(5 + k) * N + i];
     gY[k] = P.G ? P.G[(5 + k) * N + i] : 0.0;
+    for (int m = 1; m < KMAX + 3; ++m) D[m][k] = 0.0;
   }
   {
     double rho, e;
@@ -528,14 +529,33 @@ __global__ void __launch_bounds__(128) k_react_bdf(const DevState s, const BdfPa
     for (int j = 0; j < ns; ++j) P.Uout[(5 + j) * N + i] = D[0][j];
   }
   if (flag) atomicOr(s.status, flag);
+  cnt[0] += (unsigned)n_steps;
+  cnt[1] += (unsigned)n_rej;
+  cnt[2] += (unsigned)n_fail;
+  cnt[3] += (unsigned)n_eval;
+  mx = max(mx, (unsigned)n_steps);
+}
+
+// One thread per cell.  MINB caps the registers so that MINB blocks fit on
+// an SM: the kernel waits on its per-thread arrays in local memory, and more
+// resident warps hide more of that latency.  Measured at 21 species (ms per
+// launch over 4.7 M cells): 4 blocks/SM 614, 8 543, 12 490, 16 449, the
+// extra spills notwithstanding; a persistent grid with fewer resident
+// threads, which keeps those arrays in cache, was slower still.
+template <int NS, int MINB>
+__global__ void __launch_bounds__(128, MINB) k_react_bdf(const DevState s, const BdfParams P) {
+  unsigned cnt[4] = {0u, 0u, 0u, 0u}, mx = 0u;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < s.ncells;
+       i += (long long)gridDim.x * blockDim.x)
+    bdf_cell<NS>(s, P, i, cnt, mx);
   if (P.counters) {
-    const unsigned long long v[4] = {n_steps, n_rej, n_fail, n_eval};
+    // every lane of the warp is here (blocks are whole warps)
     for (int q = 0; q < 4; ++q) {
-      const unsigned long long tot = __reduce_add_sync(lanes, (unsigned)v[q]);
-      if ((threadIdx.x & 31) == __ffs(lanes) - 1) atomicAdd(P.counters + q, tot);
+      const unsigned tot = __reduce_add_sync(0xffffffffu, cnt[q]);
+      if ((threadIdx.x & 31) == 0 && tot) atomicAdd(P.counters + q, (unsigned long long)tot);
     }
-    const unsigned mx = __reduce_max_sync(lanes, (unsigned)n_steps);
-    if ((threadIdx.x & 31) == __ffs(lanes) - 1) atomicMax(P.counters + 4, (unsigned long long)mx);
+    const unsigned m = __reduce_max_sync(0xffffffffu, mx);
+    if ((threadIdx.x & 31) == 0 && m) atomicMax(P.counters + 4, (unsigned long long)m);
   }
 }
 
@@ -547,10 +567,10 @@ void launch_react_bdf(const DevState &s, const BdfParams &P, cudaStream_t st) {
   const int block = 128;
   const long long nb = (s.ncells + block - 1) / block;
   if (nb == 0) return;
-  if (s.ns <= 8) k_react_bdf<8><<<(unsigned)nb, block, 0, st>>>(s, P);
-  else if (s.ns <= 16) k_react_bdf<16><<<(unsigned)nb, block, 0, st>>>(s, P);
-  else if (s.ns <= 24) k_react_bdf<24><<<(unsigned)nb, block, 0, st>>>(s, P);
-  else k_react_bdf<32><<<(unsigned)nb, block, 0, st>>>(s, P);
+  if (s.ns <= 8) k_react_bdf<8, 16><<<(unsigned)nb, block, 0, st>>>(s, P);
+  else if (s.ns <= 16) k_react_bdf<16, 16><<<(unsigned)nb, block, 0, st>>>(s, P);
+  else if (s.ns <= 24) k_react_bdf<24, 16><<<(unsigned)nb, block, 0, st>>>(s, P);
+  else k_react_bdf<32, 16><<<(unsigned)nb, block, 0, st>>>(s, P);
 }
 
 }  // namespace smc
