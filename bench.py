@@ -611,8 +611,9 @@ def main():
         precision_report["mixed_rates32_speedup_vs_fp64"] = (runs["fp64"]["ms_step"]
                                                              / runs["mixed_rates32"]["ms_step"])
 
-    # end to end: host buffers through the C ABI, copies inside the timed region
-    Uh = U0.cpu().numpy().copy()
+    # end to end: a pinned host buffer through the C ABI, the host->device and
+    # device->host copies of every step inside the timed region
+    Uh = U0.cpu().clone().pin_memory()
     torch.cuda.empty_cache()                  # the measured runs' tensors
     h2 = smc.Smc(wl.grid, wl.mech, dict(main_opts, segment=R["tuned"]["segment"],
                                         x_layout=R["tuned"]["x_layout"],
@@ -626,7 +627,8 @@ def main():
     e2e_s = max_over_ranks(world, e2e_s, device)
     h2.close()
     e2e = {"value": world * ncells * evals_per_step / e2e_s / 1e6, "unit": "Mcell-RHS/s",
-           "h2d_bytes_per_step": nv * ncells * 8, "d2h_bytes_per_step": nv * ncells * 8}
+           "h2d_bytes_per_step": nv * ncells * 8, "d2h_bytes_per_step": nv * ncells * 8,
+           "host_buffer": "pinned"}
 
     if rank == 0:
         cpu = cpu_baseline(wl) if (world == 1 and not args.no_cpu) else None
