@@ -121,3 +121,26 @@ def test_create_rejects_unsupported_boundaries_without_touching_the_gpu(lib):
     with pytest.raises(smc.SmcError) as e:
         smc.Smc(synth.single_box((6, 8, 8), 0.1), m, x_outflow=True)
     assert "8 cells" in str(e.value)
+
+
+def test_create_rejects_bad_box_arrays_without_touching_the_gpu(lib):
+    """An empty box list, a box outside the domain, overlapping boxes and a
+    domain the boxes do not cover are refused during host validation."""
+    import numpy as np
+    from paper_1309_7327_gb300 import synth
+    m = synth.make_mechanism(3, 2, 1)
+    dx = (0.1, 0.1, 0.1)
+    cases = {
+        "no boxes": synth.Grid((8, 8, 8), dx, np.zeros((0, 3), np.int64), np.zeros((0, 3), np.int64)),
+        "outside": synth.Grid((8, 8, 8), dx, np.array([[0, 0, 0]]), np.array([[8, 7, 7]])),
+        "overlap": synth.Grid((8, 8, 8), dx, np.array([[0, 0, 0], [3, 0, 0]]),
+                              np.array([[4, 7, 7], [7, 7, 7]])),
+        "maps onto no box": synth.Grid((8, 8, 8), dx, np.array([[0, 0, 0]]),
+                                       np.array([[3, 7, 7]])),
+    }
+    for what, g in cases.items():
+        with pytest.raises(smc.SmcError) as e:
+            smc.Smc(g, m)
+        assert e.value.status == smc.SMC_ERR_ARG, what
+        assert what in str(e.value) or what == "outside" and "outside" in str(e.value), \
+            (what, str(e.value))
