@@ -29,6 +29,6 @@ Plain, slow, FP64 NumPy restatement of what the paper's method computes:
                    analytic Jacobian, and its integration by ``bdf``.
 * ``heat2d``    -- the appendix heat-equation problems T1/T2 (App. A).
 
-Where the paper is silent the readings are stated in each function and
-collected in DESIGN.md.
+Where the paper is silent the reading taken is stated in the function that
+uses it.
 """

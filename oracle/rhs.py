@@ -3,7 +3,7 @@
 
 Oracle, test infrastructure only.  Plain NumPy, FP64, no fusion.
 
-Discretisation (readings of the paper, collected in the design doc):
+Discretisation (readings of the paper where it is silent):
 
 * Convective terms: -D_d applied to the pointwise fluxes (rho u_d,
   rho u_c u_d + p delta_cd, (rho E + p) u_d, rho Y_k u_d), D the 8th-order

@@ -1,7 +1,8 @@
 """Mixture transport coefficients (oracle; test infrastructure only).
 
 The paper evaluates eta, xi, lambda and D_k with EGLIB (Sec. 5), which is
-not used here.  The stand-in model (a reading, stated in the design doc):
+not used here.  The stand-in model (a reading of the paper, which names no
+model of its own):
 
   eta      = eta_ref (T / T_ref)^eta_exp
   xi       = xi_ratio * eta                 (bulk viscosity, default 0)

@@ -203,7 +203,7 @@ def test_mode2_two_steps_graphs_and_eager_agree(smc):
     assert np.array_equal(outs[0], outs[1])
 
 
-def test_mode2_mixed_precision_within_north_star_bar(smc):
+def test_mode2_mixed_precision_within_1e5_of_fp64(smc):
     wl, U, _ = state("c1", seed=5, n=8, p_amp=0.03)
     got = {}
     for prec in (0, 1):
