@@ -135,3 +135,38 @@ def test_outflow_sdc_step(smc):
     ref = synth.global_to_boxes(grid, ref)
     err = relerr(U1 - U, ref - U)
     assert err.max() < 1e-10, err
+
+
+def test_mode2_step_with_outflow_x_ends(smc):
+    """MRSDC mode 2 (eq. mrupdate2) on a box with non-periodic x ends: the
+    advection-diffusion evaluations use the lowered stencils, the implicit
+    reaction integration is pointwise; against the oracle's mode-2 step."""
+    from oracle import react
+    grid, mech, U_g = flame_box(n=(16, 8, 8), ns=3, nr=2, seed=4)
+    U = synth.global_to_boxes(grid, U_g)
+    dt = 2e-9
+    rtol, atol = 1e-10, 1e-14
+    with smc.Smc(grid, mech, {"mr_mode": 2, "bdf_rtol": rtol, "bdf_atol": atol},
+                 x_outflow=True) as h:
+        Ud = dev(U)
+        h.sdc_step(Ud, dt, nodes=3, sweeps=2, reaction_substeps=3)
+        h.synchronize()
+        got = Ud.cpu().numpy()
+    o = orhs.Options(x_outflow=True)
+
+    def fA(u):
+        return orhs.rhs_periodic(u, mech, grid.dx, o, parts=True)[0]
+
+    def fR(u):
+        return orhs.rhs_periodic(u, mech, grid.dx, o, parts=True)[1]
+
+    def integ(Up, G, dtp):
+        return react.integrate(Up, G, dtp, mech, rtol=rtol, atol=atol)
+
+    ref, _, _, _, _ = osdc.mrsdc2_step(U_g, fA, fR, integ, dt, coarse=3, fine=3, sweeps=2,
+                                       species=slice(5, 5 + mech.ns))
+    ref = synth.global_to_boxes(grid, ref)
+    ratio = np.max(np.abs(got[5:] - ref[5:]) / (rtol * np.abs(ref[5:]) + atol * U[0][None]))
+    assert ratio < 1e-2, ratio
+    err = relerr(got[:5] - U[:5], ref[:5] - U[:5])
+    assert err.max() < 1e-6, err
