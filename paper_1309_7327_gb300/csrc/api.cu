@@ -751,8 +751,11 @@ smc_status sdc_multirate2(smc_handle *h, double *U, const void *key, double dt, 
         cr.src[cr.nsrc++] = h->rpool[Rtold[p + 1]];
         launch_combo(G + 5 * N, G + 5 * N, cr, nsN, h->stream);
       }
+      // R(U_p) is known: R(U_0) in slot 0, then the previous interval's end value
+      const double *R_p = h->rpool[F1new[p]];
       {
-        const BdfParams P = bdf_params(h, Up, G, dtp, Rt1, nullptr);
+        BdfParams P = bdf_params(h, Up, G, dtp, Rt1, nullptr);
+        P.F0 = R_p;
         Timed t(h, SMC_K_BDF);
         launch_react_bdf(s, P, h->stream);
       }
@@ -807,7 +810,8 @@ smc_status sdc_multirate2(smc_handle *h, double *U, const void *key, double dt, 
         launch_combo(G, G, co, n, h->stream);
       }
       {
-        const BdfParams P = bdf_params(h, Up, G, dtp, h->rpool[Rtnew[p + 1]], U);
+        BdfParams P = bdf_params(h, Up, G, dtp, h->rpool[Rtnew[p + 1]], U);
+        P.F0 = R_p;
         Timed t(h, SMC_K_BDF);
         launch_react_bdf(s, P, h->stream);
       }

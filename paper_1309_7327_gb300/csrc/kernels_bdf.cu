@@ -384,8 +384,14 @@ __device__ __forceinline__ void bdf_cell(const DevState &s, const BdfParams &P, 
       wantJ = fresh;
       it = 0;
     }
-    const bool ok = ode_eval<NS>(s, c, tau, yv, gY, f, wantJ ? J : nullptr);
-    ++n_eval;
+    bool ok = true;
+    if (phase == PH_F0 && P.F0) {
+      // f(0, y_0) = R(U_0) + G_Y from the caller's reaction rates at U_0
+      for (int j = 0; j < ns; ++j) f[j] = P.F0[(long long)j * N + i] + gY[j];
+    } else {
+      ok = ode_eval<NS>(s, c, tau, yv, gY, f, wantJ ? J : nullptr);
+      ++n_eval;
+    }
     if (phase == PH_F0 || phase == PH_F1) {
       if (!ok) {
         flag |= ST_NONCONV;

@@ -238,6 +238,7 @@ void launch_exp(const Mech *m, const double *x, double *y, long long n, cudaStre
 struct BdfParams {
   const double *U;                // [nv][ncells] state at tau = 0
   const double *G;                // [nv][ncells] constant forcing, or null (zero)
+  const double *F0;               // [ns][ncells] R(U) at tau = 0 if known, or null
   double *Rbar;
   double *Uout;
   unsigned long long *counters;   // [5]: steps, rejected, Newton failures, evaluations,
