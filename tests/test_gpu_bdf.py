@@ -124,20 +124,21 @@ def _mode2_oracle(wl, U_g, dt, coarse, fine, sweeps, repeat=1, eps=0.0, history=
                             repeat=repeat, species=slice(5, 5 + ns), eps=eps, history=history)
 
 
-@pytest.mark.parametrize("fine,sweeps", [(3, 2), (2, 3)])
-def test_mode2_step_matches_oracle(smc, fine, sweeps):
+@pytest.mark.parametrize("nodes,fine,sweeps", [(3, 3, 2), (3, 2, 3), (5, 2, 2)])
+def test_mode2_step_matches_oracle(smc, nodes, fine, sweeps):
     wl, U, U_g = state("c1", seed=3, n=8, p_amp=0.03)
     dt = wl.dt
     with smc.Smc(wl.grid, wl.mech, _opts(mr_mode=2)) as h:
         Ud = dev(U)
-        h.sdc_step(Ud, dt, nodes=3, sweeps=sweeps, reaction_substeps=fine)
+        h.sdc_step(Ud, dt, nodes=nodes, sweeps=sweeps, reaction_substeps=fine)
         h.synchronize()
         st = h.stats()
         got = Ud.cpu().numpy()
-    ref, _, _, nA, nR = _mode2_oracle(wl, U_g, dt, 3, fine, sweeps)
+    ref, _, _, nA, nR = _mode2_oracle(wl, U_g, dt, nodes, fine, sweeps)
     ref = synth.global_to_boxes(wl.grid, ref)
-    M2 = 2 * (fine - 1)
-    assert (st["n_rhs"], st["n_react"]) == (nA, nR) == (sweeps * M2 + 1, sweeps * 2 + 1)
+    M1 = nodes - 1
+    M2 = M1 * (fine - 1)
+    assert (st["n_rhs"], st["n_react"]) == (nA, nR) == (sweeps * M2 + 1, sweeps * M1 + 1)
     assert tol_ratio(got[5:], ref[5:], U[0][None]) < 1e-2
     err = relerr(got[:5] - U[:5], ref[:5] - U[:5])
     assert err.max() < 1e-7, err
