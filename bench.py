@@ -213,9 +213,25 @@ def measured_peaks():
         return {}
 
 
-def cpu_baseline(wl, budget_s: float = 15.0):
+def _oracle_worker(job):
+    """One host process evaluating the oracle's right-hand side on a patch for
+    `budget` seconds; returns (evaluations, seconds)."""
+    patch, mech, dx, budget = job
+    from oracle import rhs as orhs
+    evals, t0 = 0, time.perf_counter()
+    while True:
+        orhs.rhs_ghosted(patch, mech, dx)
+        evals += 1
+        el = time.perf_counter() - t0
+        if el > budget:
+            return evals, el
+
+
+def cpu_baseline(wl, budget_s: float = 15.0, all_cores_s: float = 0.0):
     """The oracle's right-hand side on a bounded sample of the workload's boxes
-    (host cores, NumPy, single thread)."""
+    (host cores, NumPy, single thread).  all_cores_s > 0: the same sample on
+    every host core at once as well (one spawned process per core, each for
+    that many seconds), reported beside the single-thread figure."""
     import numpy as np
 
     from oracle import rhs as orhs
@@ -242,10 +258,26 @@ def cpu_baseline(wl, budget_s: float = 15.0):
         el = time.perf_counter() - t0
         if el > budget_s or evals >= 50:
             break
-    return {"value": cells * evals / el / 1e6, "unit": "Mcell-RHS/s", "cores": 1,
-            "kind": "oracle",
-            "sample": f"{evals} full RHS evaluations of {cells} cells of box {b} of workload "
-                      f"{wl.name} by the NumPy FP64 oracle, {el:.1f} s"}
+    out = {"value": cells * evals / el / 1e6, "unit": "Mcell-RHS/s", "cores": 1,
+           "kind": "oracle",
+           "sample": f"{evals} full RHS evaluations of {cells} cells of box {b} of workload "
+                     f"{wl.name} by the NumPy FP64 oracle, {el:.1f} s"}
+    if all_cores_s > 0:
+        # spawned (not forked) processes: the parent may hold a CUDA context;
+        # a worker that cannot start ends the pool with an error, not a hang
+        import concurrent.futures as cf
+        import multiprocessing as mp
+        n = os.cpu_count() or 1
+        try:
+            with cf.ProcessPoolExecutor(n, mp_context=mp.get_context("spawn")) as ex:
+                res = list(ex.map(_oracle_worker, [(patch, wl.mech, g.dx, all_cores_s)] * n,
+                                  timeout=120 + 4 * all_cores_s))
+            out["all_cores"] = {"value": sum(cells * e / t for e, t in res) / 1e6, "cores": n,
+                                "sample": f"the same patch on {n} processes at once, "
+                                          f"{all_cores_s:.0f} s each"}
+        except Exception as e:                        # reported, never fatal
+            out["all_cores"] = {"unavailable": f"{type(e).__name__}: {e}"[:200]}
+    return out
 
 
 def bench_config(wl, args, main_key, world):
@@ -631,7 +663,7 @@ def main():
            "host_buffer": "pinned"}
 
     if rank == 0:
-        cpu = cpu_baseline(wl) if (world == 1 and not args.no_cpu) else None
+        cpu = cpu_baseline(wl, all_cores_s=8.0) if (world == 1 and not args.no_cpu) else None
         line = {
             "metric": "Mcell-RHS/s (21 species)", "value": value, "unit": "Mcell-RHS/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
