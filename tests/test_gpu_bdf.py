@@ -227,3 +227,25 @@ def test_mode2_and_integrator_reject_more_than_32_species(smc):
             h.react_integrate(Z, None, 1e-8, Z)
         with pytest.raises(smc.SmcError):
             h.sdc_step(Z, 1e-8, nodes=3, sweeps=1, reaction_substeps=3)
+
+
+def test_react_integrate_30_species(smc):
+    """The 25-32-species instance of the integrator (30 species, 60
+    reactions) on a small box, sampled cells against the oracle."""
+    grid = synth.single_box((8, 8, 4), 1.0 / 64)
+    mech = synth.make_mechanism(30, 60, 5)
+    prim = synth.global_to_boxes(grid, synth.smooth_fields(grid, 30, 105, T0=1400.0, T1=200.0,
+                                                            umax=3000.0))
+    U = thermo.conserved(prim, mech.nasa7, mech.W)
+    dt = 2e-7
+    with smc.Smc(grid, mech, _opts()) as h:
+        Ud = dev(U)
+        out = torch.empty_like(Ud)
+        h.react_integrate(Ud, None, dt, out)
+        h.synchronize()
+        got = out.cpu().numpy()
+    cells = [0, 37, 101, 200, 255]
+    ref = react.integrate(U, None, dt, mech, rtol=RTOL, atol=ATOL, cells=cells)
+    assert np.abs(ref[5:] - U[5:, cells]).max() > 1e4 * RTOL * np.abs(U[5:]).max()
+    assert tol_ratio(got[5:, cells], ref[5:], U[0][None, cells]) < 1e-2
+    assert np.abs(got[5:].sum(0) - got[0]).max() <= 1e-12 * got[0].max()
