@@ -639,6 +639,20 @@ def main():
                         for k, r in runs.items()}
     if "mixed" in runs and "fp64" in runs:
         precision_report["mixed_speedup_vs_fp64"] = runs["fp64"]["ms_step"] / runs["mixed"]["ms_step"]
+        # the error that speedup comes at: one right-hand side of the initial
+        # state in each precision, per component max|F_mixed - F_fp64| / max|F_fp64|
+        torch.cuda.empty_cache()
+        Ud = U0.to(device)
+        F = {}
+        for key, prec in (("fp64", 0), ("mixed", 1)):
+            with smc.Smc(wl.grid, wl.mech, {"precision": prec}, x_outflow=wl.x_outflow) as he:
+                F[key] = torch.empty_like(Ud)
+                he.rhs(Ud, F[key])
+                he.synchronize()
+        num = (F["mixed"] - F["fp64"]).abs().amax(dim=1)
+        den = F["fp64"].abs().amax(dim=1).clamp_min(1e-300)
+        precision_report["mixed_rhs_error_vs_fp64"] = float((num / den).max())
+        del Ud, F
     if "mixed_rates32" in runs and "fp64" in runs:
         precision_report["mixed_rates32_speedup_vs_fp64"] = (runs["fp64"]["ms_step"]
                                                              / runs["mixed_rates32"]["ms_step"])
