@@ -33,6 +33,16 @@ Discretisation (readings of the paper where it is silent):
   for k != ref, F_ref = -sum_{k != ref} F_k, and the energy flux uses
   h_k - h_ref.
 * Chemistry: rho omega_k from ``chem.production_rates``.
+* Options.terms selects which groups of terms are added (all by default), so
+  that each can be checked on its own against the continuous operator:
+    "conv"  -div of the convective fluxes (every component),
+    "visc"  div tau (momentum),
+    "work"  div(tau . u) (energy),
+    "heat"  div(lambda grad T) (energy),
+    "diff"  -div Fbar_k (species) and -div sum_k Fbar_k h_k (energy); in
+            reference-species mode the whole species diffusion,
+    "vc"    the correction-velocity terms div(Y_k V_c), div(h V_c),
+    "chem"  rho omega_k.
 * Non-periodic x ends (Options.x_outflow): every x derivative -- convective,
   narrow, mixed, velocity gradients, correction velocity -- uses the
   boundary-lowered stencils of ``stencil.D_bc`` / ``stencil.narrow_bc`` in
@@ -61,6 +71,7 @@ class Options:
     T0: float = 1000.0              # Newton first guess
     reactions: bool = True
     x_outflow: bool = False         # x ends are non-periodic boundaries (lowered stencils)
+    terms: frozenset = frozenset(("conv", "visc", "work", "heat", "diff", "vc", "chem"))
 
 
 def _inner(f, dirs):
@@ -99,6 +110,7 @@ def rhs_ghosted(Ug: np.ndarray, mech, dx, opt: Options | None = None,
     B = rhoD * (X - Y) / p[None]
     M = stencil.to_float(stencil.narrow8_exact(opt.m47, opt.m48), Ug.dtype)
 
+    terms = opt.terms
     interior = _inner(_inner(_inner(Ug, [0]), [1]), [2]).shape
     out = np.zeros(interior, dtype=Ug.dtype)
     Nsum = np.zeros((ns,) + interior[1:], dtype=Ug.dtype)
@@ -131,49 +143,56 @@ def rhs_ghosted(Ug: np.ndarray, mech, dx, opt: Options | None = None,
 
         ud = vel[d]
         # convective fluxes
-        out[0] -= Dd(lin(Ug[1 + d]))
-        for c in range(3):
-            flux = Ug[1 + c] * ud + (p if c == d else 0.0)
-            out[1 + c] -= Dd(lin(flux))
-        out[4] -= Dd(lin((Ug[4] + p) * ud))
-        out[5:] -= Dd(lin(Ug[5:] * ud[None]))
+        if "conv" in terms:
+            out[0] -= Dd(lin(Ug[1 + d]))
+            for c in range(3):
+                flux = Ug[1 + c] * ud + (p if c == d else 0.0)
+                out[1 + c] -= Dd(lin(flux))
+            out[4] -= Dd(lin((Ug[4] + p) * ud))
+            out[5:] -= Dd(lin(Ug[5:] * ud[None]))
 
         # viscous stress
         Gee, Gff = grad(e, e), grad(f, f)
         Ged, Gfd = grad(d, e), grad(d, f)
-        out[1 + d] += nd(c43, vel[d]) + Dd(lin(c23) * (Gee + Gff))
-        out[1 + e] += nd(eta, vel[e]) + Dd(lin(eta) * Ged)
-        out[1 + f] += nd(eta, vel[f]) + Dd(lin(eta) * Gfd)
-        out[4] += nd(c43, 0.5 * vel[d] ** 2) + nd(eta, 0.5 * (vel[e] ** 2 + vel[f] ** 2))
-        out[4] += Dd(lin(c23) * (Gee + Gff) * lin(vel[d])
-                     + lin(eta) * Ged * lin(vel[e]) + lin(eta) * Gfd * lin(vel[f]))
+        if "visc" in terms:
+            out[1 + d] += nd(c43, vel[d]) + Dd(lin(c23) * (Gee + Gff))
+            out[1 + e] += nd(eta, vel[e]) + Dd(lin(eta) * Ged)
+            out[1 + f] += nd(eta, vel[f]) + Dd(lin(eta) * Gfd)
+        if "work" in terms:
+            out[4] += nd(c43, 0.5 * vel[d] ** 2) + nd(eta, 0.5 * (vel[e] ** 2 + vel[f] ** 2))
+            out[4] += Dd(lin(c23) * (Gee + Gff) * lin(vel[d])
+                         + lin(eta) * Ged * lin(vel[e]) + lin(eta) * Gfd * lin(vel[f]))
         # heat conduction
-        out[4] += nd(lam, T)
+        if "heat" in terms:
+            out[4] += nd(lam, T)
 
         # species diffusion
         if opt.mode == "vc":
             Nd = nd(rhoD, X) + nd(B, p[None])
             Nsum += Nd
-            out[5:] += Nd
-            out[4] += np.sum(nd(rhoD * h, X), axis=0) + nd(np.sum(h * B, axis=0), p)
+            if "diff" in terms:
+                out[5:] += Nd
+                out[4] += np.sum(nd(rhoD * h, X), axis=0) + nd(np.sum(h * B, axis=0), p)
             rD_c = _inner(rhoD, [d])
             B_c = _inner(B, [d])
             Vc = -(np.sum(_inner(rD_c, [e, f]) * Dd(lin(X)), axis=0)
                    + np.sum(_inner(B_c, [e, f]), axis=0) * Dd(lin(p)))
-            out[5:] += Dd(lin(Y)) * Vc[None]
-            out[4] += Dd(lin(hmix)) * Vc
+            if "vc" in terms:
+                out[5:] += Dd(lin(Y)) * Vc[None]
+                out[4] += Dd(lin(hmix)) * Vc
         elif opt.mode == "ref":
             hr = h - h[ref][None]
             keep = [k for k in range(ns) if k != ref]
-            Nd = nd(rhoD[keep], X[keep]) + nd(B[keep], p[None])
-            out[5 + np.array(keep)] += Nd
-            out[5 + ref] -= np.sum(Nd, axis=0)
-            out[4] += (np.sum(nd(rhoD[keep] * hr[keep], X[keep]), axis=0)
-                       + nd(np.sum(hr[keep] * B[keep], axis=0), p))
+            if "diff" in terms:
+                Nd = nd(rhoD[keep], X[keep]) + nd(B[keep], p[None])
+                out[5 + np.array(keep)] += Nd
+                out[5 + ref] -= np.sum(Nd, axis=0)
+                out[4] += (np.sum(nd(rhoD[keep] * hr[keep], X[keep]), axis=0)
+                           + nd(np.sum(hr[keep] * B[keep], axis=0), p))
         else:
             raise ValueError(opt.mode)
 
-    if opt.mode == "vc":
+    if opt.mode == "vc" and "vc" in terms:
         divVc = -np.sum(Nsum, axis=0)
         Yi = _inner(_inner(_inner(Y, [0]), [1]), [2])
         hi = _inner(_inner(_inner(hmix, [0]), [1]), [2])
@@ -181,7 +200,7 @@ def rhs_ghosted(Ug: np.ndarray, mech, dx, opt: Options | None = None,
         out[4] += hi * divVc
 
     ch = np.zeros(interior, dtype=Ug.dtype)
-    if opt.reactions and mech.A.shape[0] > 0:
+    if opt.reactions and "chem" in terms and mech.A.shape[0] > 0:
         ri = _inner(_inner(_inner(rho, [0]), [1]), [2])
         Ti = _inner(_inner(_inner(T, [0]), [1]), [2])
         Yi = _inner(_inner(_inner(Y, [0]), [1]), [2])
