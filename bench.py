@@ -12,10 +12,16 @@ domain, 21 species / 84 reactions, multirate SDC with 3 coarse
 value = cells x advection-diffusion RHS evaluations per step / time (Mcell-RHS/s),
 with K M1 = 8 such evaluations per multirate step after the first (the
 first value f(U_0) is recycled, Sec. 3.1); the K M2 reaction evaluations of
-the fine nodes are part of the step's time.
+the fine nodes are part of the step's time.  The headline is the FP64 path
+(the paper's precision); the mixed FP32/FP64 path and its error are reported
+beside it under "precisions".
+
+Arithmetic rooflines divide by FMA-pipe throughputs measured on the same GPU
+in the same run (smc_fma_throughput), HBM ones by the measured copy
+bandwidth of MEASURED_PEAKS.json.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl smc|reference]
-                       [--workload c4] [--precision fp64]
+                       [--workload c1|c2|c3|c4|c5|t1|t2|peaks] [--precision fp64]
 """
 from __future__ import annotations
 
@@ -32,8 +38,6 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-SM_COUNT = 152
-
 
 def parse():
     ap = argparse.ArgumentParser()
@@ -42,8 +46,12 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="smc", choices=["smc", "reference"])
     ap.add_argument("--workload", default="c4")
-    ap.add_argument("--precision", default="both", choices=["fp64", "mixed", "mixed_rates32", "both"],
-                    help="both: the mixed path is the headline, FP64 measured beside it")
+    ap.add_argument("--precision", default="both",
+                    choices=["fp64", "mixed", "mixed_rates32", "both", "fp64+mixed"],
+                    help="both: FP64 is the headline, mixed and mixed with FP32-mantissa rates "
+                         "measured beside it; fp64+mixed: the first two only")
+    ap.add_argument("--lean", action="store_true",
+                    help="skip the kernel-by-kernel (no graph) timing pass (long-step workloads)")
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--n", type=int, default=None,
                     help="smaller instance of the workload (profiling captures)")
@@ -213,6 +221,58 @@ def measured_peaks():
         return {}
 
 
+def pipe_peaks(local: int) -> dict:
+    """FMA-pipe throughputs of this GPU, measured now by smc_fma_throughput
+    (FP64, FP32, paired FP32), with the SM clock sampled while they run.
+    Iteration counts give about 0.3 s per pipe at the expected rates."""
+    from paper_1309_7327_gb300 import smc
+    sampler = ClockSampler(local)
+    sampler.start()
+    out = {}
+    for name, kind, iters in (("fp64", 0, 150_000), ("fp32", 1, 8_000_000),
+                              ("fp32x2", 2, 4_000_000)):
+        smc.smc_fma_throughput(kind, max(1, iters // 10))
+        fl, ms, sms = smc.smc_fma_throughput(kind, iters)
+        out[name + "_tflops"] = fl / 1e12
+        out[name + "_ms"] = ms
+        out["sm_count"] = sms
+    out["clocks"] = sampler.stop()
+    out["how"] = ("smc_fma_throughput: sm_count x 4 blocks x 256 threads, 8 independent FMA "
+                  "chains per thread, CUDA events, after one untimed launch")
+    return out
+
+
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from
+# ncu captures, keyed by (kernel, precision, workload): value, the capture it
+# came from, and the SHA-256 (first 16 hex digits) of every source file the
+# kernel is compiled from at the time of the capture.  A mismatch (the kernel
+# changed since) makes the bench report traffic null.
+NCU_TRAFFIC = {}
+
+
+def _sources_digest(files) -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for f in files:
+        with open(os.path.join(ROOT, "paper_1309_7327_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel: str, precision: str, workload: str, ncells_launch: float):
+    """Measured DRAM bytes of one launch of `kernel` on this workload, or None
+    when there is no capture or the kernel's sources changed since it."""
+    e = NCU_TRAFFIC.get((kernel, precision, workload))
+    if not e:
+        return None
+    try:
+        if _sources_digest(e["files"]) != e["digest"]:
+            return None
+    except OSError:
+        return None
+    return e["bytes_per_cell"] * ncells_launch
+
+
 def _oracle_worker(job):
     """One host process evaluating the oracle's right-hand side on a patch for
     `budget` seconds; returns (evaluations, seconds)."""
@@ -322,7 +382,7 @@ def run_reference(args):
         return
     from paper_1309_7327_gb300 import synth
     wl = synth.workload(args.workload, seed=args.seed, n=args.n)
-    main_key = {"both": "mixed"}.get(args.precision, args.precision)
+    main_key = {"both": "fp64", "fp64+mixed": "fp64"}.get(args.precision, args.precision)
     for _ in range(args.warmup):
         cpu_baseline(wl, budget_s=1.0)
     vals = []
@@ -385,17 +445,11 @@ def run_heat(args):
     # takes two faces (x, y), two face differences, one sum (+ the source)
     face = 7 + 2 * (44 + 8)
     flops_eval = N * N * (2 * face + 3 + (2 if G is not None else 0))
-    sm_mhz = clocks.get("sm_mhz") or 2070.0
-    fp64_peak = SM_COUNT * 4 * sm_mhz * 1e6
+    pk = pipe_peaks(0)
+    fp64_peak = pk["fp64_tflops"] * 1e12
     fl_s = flops_eval * evals / (ms / 1e3)
     # ncu DRAM bytes of one k_heat_rhs launch (a 2048^2 capture scaled by cells)
-    heat_traffic = None
-    try:
-        db = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
-        if "k_heat_rhs:t1" in db:
-            heat_traffic = db["k_heat_rhs:t1"] * (N * N) / (4096 * 4096)
-    except (OSError, ValueError):
-        pass
+    heat_traffic = ncu_traffic("k_heat_rhs", "fp64", args.workload, N * N)
     line = {"metric": f"Mcell-RHS/s (heat {args.workload.upper()})", "value": value,
             "unit": "Mcell-RHS/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -407,12 +461,13 @@ def run_heat(args):
                                                     "the evaluations",
                          "achieved": fl_s / 1e12, "peak": fp64_peak / 1e12, "unit": "TFLOP/s",
                          "frac": fl_s / fp64_peak, "traffic": None,
-                         "peak_source": "FP64 pipe: 152 SMs x 2 FMA/clk x median SM clock under load"},
+                         "peak_source": "FP64 pipe, measured in this run by smc_fma_throughput "
+                                        "(of measured)"},
             "hbm": {"kernel": "whole step", "algorithmic_bytes_per_step": N * N * per_step,
                     "achieved_gbs": bytes_ / (ms / 1e3) / 1e9, "peak_gbs": peak,
                     "frac": bytes_ / (ms / 1e3) / 1e9 / peak,
                     "k_heat_rhs_dram_bytes_per_launch": heat_traffic},
-            "clocks": clocks, "gpu_launches": int(2 * evals)}
+            "clocks": clocks, "pipe_peaks": pk, "gpu_launches": int(2 * evals)}
     print(json.dumps(line))
 
 
@@ -423,6 +478,18 @@ def main():
         return
     if args.workload in ("t1", "t2"):
         run_heat(args)
+        return
+    if args.workload == "peaks":
+        import torch
+
+        import __graft_entry__
+        __graft_entry__.build()
+        torch.cuda.set_device(0)
+        pk = pipe_peaks(0)
+        print(json.dumps({"metric": "FMA pipe throughput", "value": pk["fp64_tflops"],
+                          "unit": "TFLOP/s (FP64)", "n_gpus": 1, "higher_is_better": True,
+                          "data": "synthetic", "config": {"workload": "peaks"}, "pipe_peaks": pk,
+                          "hbm_gbs": measured_peaks().get("hbm_gbs")}))
         return
     import numpy as np
     import torch
@@ -528,24 +595,28 @@ def main():
         h.set_option("profile", 0)
         # the same steps launched kernel by kernel (no graph replay), timed
         # like the graph-replayed ones: what the graph capture saves
-        h.set_option("use_graphs", 0)
-        h.sdc_step(U, wl.dt, nodes, sweeps, rsub)
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        torch.cuda.synchronize(device)
-        e0.record(stream)
-        for _ in range(args.steps):
+        ms_eager = None
+        if not args.lean:
+            h.set_option("use_graphs", 0)
             h.sdc_step(U, wl.dt, nodes, sweeps, rsub)
-        e1.record(stream)
-        torch.cuda.synchronize(device)
-        ms_eager = e0.elapsed_time(e1) / args.steps
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize(device)
+            e0.record(stream)
+            for _ in range(args.steps):
+                h.sdc_step(U, wl.dt, nodes, sweeps, rsub)
+            e1.record(stream)
+            torch.cuda.synchronize(device)
+            ms_eager = e0.elapsed_time(e1) / args.steps
         h.close()
         return dict(ms_step=ms / args.steps, launches=launches, kms=st2["kernel_ms"],
                     clocks=clocks, U0=U0, tuned=tuned, ms_eager=ms_eager, evals=evals_done,
                     bdf_evals=bdf_evals)
 
+    pk = pipe_peaks(local)                    # FMA-pipe denominators, measured now
     runs = {}
-    order = {"both": ["mixed", "fp64", "mixed_rates32"]}.get(args.precision, [args.precision])
+    order = {"both": ["fp64", "mixed", "mixed_rates32"],
+             "fp64+mixed": ["fp64", "mixed"]}.get(args.precision, [args.precision])
     for name in order:
         runs[name] = measure(name)
     main_key = order[0]
@@ -558,28 +629,26 @@ def main():
 
     # rooflines of the two heaviest kernels; "roofline" is the one with the
     # larger share of the step
-    sm_mhz = clocks.get("sm_mhz") or 2070.0
-    fp64_peak = SM_COUNT * 4 * sm_mhz * 1e6          # 2 DFMA / clk / SM (1.25 TFLOP/s at 2.07 GHz)
-    fp32_peak = SM_COUNT * 256 * sm_mhz * 1e6        # 128 FP32 FMA / clk / SM
-    prof = os.path.join(ROOT, "profiles", "traffic.json")
-    try:
-        traffic_db = json.load(open(prof))
-    except (OSError, ValueError):
-        traffic_db = {}
+    fp64_peak = pk["fp64_tflops"] * 1e12
+    # the mixed line kernels issue paired FP32 FMAs: their pipe peak is the
+    # larger of the plain and paired measurements
+    fp32_peak = max(pk["fp32_tflops"], pk["fp32x2_tflops"]) * 1e12
+    src64 = "FP64 pipe, measured in this run by smc_fma_throughput (of measured)"
+    src32 = "FP32 pipe (paired FMAs), measured in this run by smc_fma_throughput (of measured)"
     rooflines = {}
     n_march = launches["march"]
     if n_march:
         march_ms = kms["march"] / n_march
         if main_opts["precision"] == 0:
-            fl, peak, src = march_flops_per_cell(wl.mech.ns) * ncells, fp64_peak, "FP64 pipe"
+            fl, peak, src = march_flops_per_cell(wl.mech.ns) * ncells, fp64_peak, src64
         else:
-            fl, peak, src = march_flops_per_cell_mixed(wl.mech.ns) * ncells, fp32_peak, "FP32 pipe"
+            fl, peak, src = march_flops_per_cell_mixed(wl.mech.ns) * ncells, fp32_peak, src32
         rooflines["k_march"] = {
             "bound": "alu", "kernel": "k_march (one stencil direction)",
             "achieved": fl / (march_ms / 1e3) / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s",
             "frac": fl / (march_ms / 1e3) / peak,
-            "traffic": traffic_db.get(f"k_march:{main_key}:{args.workload}"),
-            "peak_source": f"{src}: 152 SMs x FMA/clk x median SM clock under load",
+            "traffic": ncu_traffic("k_march", main_key, args.workload, ncells),
+            "peak_source": src,
             "share": kms["march"] / max(sum(kms.values()), 1e-9)}
         # the same kernel against HBM: algorithmic bytes = every primitive
         # plane read once over the ghosted cells plus the accumulator written
@@ -603,8 +672,8 @@ def main():
             "bound": "alu", "kernel": "k_fine_chain (reaction substeps of one coarse interval)",
             "achieved": fl / (fine_ms / 1e3) / 1e12, "peak": fp64_peak / 1e12, "unit": "TFLOP/s",
             "frac": fl / (fine_ms / 1e3) / fp64_peak,
-            "traffic": traffic_db.get(f"k_fine_chain:{main_key}:{args.workload}"),
-            "peak_source": "FP64 pipe: 152 SMs x 2 FMA/clk x median SM clock under load",
+            "traffic": ncu_traffic("k_fine_chain", main_key, args.workload, ncells),
+            "peak_source": src64,
             "share": kms["fine"] / max(sum(kms.values()), 1e-9)}
     if launches.get("bdf"):
         bdf_ms = kms["bdf"] / launches["bdf"]
@@ -616,7 +685,7 @@ def main():
             "frac": fl / (bdf_ms / 1e3) / fp64_peak, "traffic": None,
             "note": "production-rate flops of the counted evaluations only (Jacobian, LU and "
                     "temperature solves not counted): a lower bound",
-            "peak_source": "FP64 pipe: 152 SMs x 2 FMA/clk x median SM clock under load",
+            "peak_source": src64,
             "share": kms["bdf"] / max(sum(kms.values()), 1e-9)}
     roofline = max(rooflines.values(), key=lambda r: r["share"]) if rooflines else None
     # HBM-bound stage: SDC / fine-node updates
@@ -632,6 +701,22 @@ def main():
                "note": "algorithmic bytes; the chain also evaluates reactions in FP64"}
     else:
         hbm = None
+    # the fused right-hand side alone (every stage of one evaluation: gather,
+    # primitives, transport, stencils, correction terms, reactions) against
+    # HBM: its algorithmic bytes are U read once and dUdt written once
+    rhs_ms = R["tuned"]["rhs_ms_tuned"]
+    rhs_bytes = 2 * nv * 8 * ncells
+    rhs_stage = {"ms_per_evaluation": rhs_ms, "algorithmic_bytes": rhs_bytes,
+                 "achieved_gbs": rhs_bytes / (rhs_ms / 1e3) / 1e9,
+                 "peak_gbs": hbm_peak, "frac_hbm": rhs_bytes / (rhs_ms / 1e3) / 1e9 / hbm_peak,
+                 "note": "one full RHS evaluation (CUDA events, autotuned schedule); the stage is "
+                         "bound by the FP64 (or FP32) pipe, not by HBM: see rooflines"}
+    mode2_note = None
+    if args.mr_mode == 2:
+        mode2_note = ("MRSDC mode 2 sweeps converge while |r| dt_p <= ~250 (r the reaction "
+                      "eigenvalue, dt_p the coarse interval); with the paper's Lobatto nodes the "
+                      "converged sweeps are accurate only while |r| dt_p is a few (A- but not "
+                      "L-stable collocation)")
     precision_report = {k: {"value": world * ncells * evals_per_step / (r["ms_step"] / 1e3) / 1e6,
                             "ms_per_step": r["ms_step"], "autotuned": r["tuned"],
                             "ms_per_step_without_graphs": r["ms_eager"],
@@ -685,12 +770,15 @@ def main():
             "dtype": "f64" if main_key == "fp64" else "f32+f64",
             "data": "synthetic",
             "config": bench_config(wl, args, main_key, world),
-            "roofline": roofline, "rooflines": rooflines, "hbm": hbm, "cpu_baseline": cpu, "e2e": e2e,
+            "roofline": roofline, "rooflines": rooflines, "hbm": hbm, "rhs_stage": rhs_stage,
+            "pipe_peaks": pk, "cpu_baseline": cpu, "e2e": e2e,
             "precisions": precision_report,
             "gpu_launches": int(sum(launches.values())),
             "kernel_ms_per_step": {k: kms[k] / args.steps for k in kms},
             "clocks": clocks,
         }
+        if mode2_note:
+            line["mode2_stiffness_bound"] = mode2_note
         print(json.dumps(line))
     if world > 1:
         import torch.distributed as dist

@@ -293,22 +293,24 @@ smc_status smc_multirate_collocation(int coarse, int fine, int repeat, double *t
 
 /* The FP64 right-hand side of smc_rhs for ONE triply periodic box of
  * n[0] x n[1] x n[2] cells (spacing dx, cm) without any device allocation.
- * The paper has no counterpart: this entry point exists for callers that
- * cannot call cudaMalloc -- code inside CUDA stream capture, applications
- * whose framework owns all device memory in a fixed arena, and loops that
- * must not pay the implicit synchronisation of cudaMalloc/cudaFree.
- * U and dUdt are caller-owned device arrays in the box layout; mech is host
- * memory.  Default options (correction-velocity mode, default stencil
+ * The paper has no counterpart.  It exists for callers that cannot call
+ * cudaMalloc: applications whose framework owns all device memory in a fixed
+ * arena, and loops that must not pay the implicit synchronisation of
+ * cudaMalloc/cudaFree.
+ * U and dUdt are caller-owned arrays in the box layout, device memory of the
+ * current device (SMC_ERR_ARG otherwise: there is no host staging); mech is
+ * host memory.  Default options (correction-velocity mode, default stencil
  * parameters, reactions on).  All scratch, tables and constants live in one
  * static device array of 20 MiB that every GPU loading the library reserves
  * until the process exits; a box whose scratch would not fit (about 16^3
- * cells with 21 species, 24^3 with 3) returns SMC_ERR_ARG.  The first call
- * on a device looks up that array's address (cudaGetSymbolAddress) and
- * should come before any stream capture.  Tables are copied from host
- * memory with cudaMemcpyAsync on `stream` (a cudaStream_t, NULL = default)
- * and the call returns after the stream has finished, with the device
- * status of the evaluation.  Calls share the array: calls that overlap on
- * the GPU race and must be serialised by the caller. */
+ * cells with 21 species, 24^3 with 3), or with a side above 65536, returns
+ * SMC_ERR_ARG.  The first call on a device looks up that array's address
+ * (cudaGetSymbolAddress).  Tables are copied from host memory with
+ * cudaMemcpyAsync on `stream` (a cudaStream_t, NULL = default) and the call
+ * waits for the stream and returns the device status of the evaluation, so
+ * it cannot be issued while `stream` is being captured into a CUDA graph.
+ * Calls share the array and it keeps the last call's contents: calls that
+ * overlap on the GPU race and must be serialised by the caller. */
 smc_status smc_rhs_noalloc(const int n[3], const double dx[3], const smc_mechanism *mech,
                            const double *U, double *dUdt, void *stream);
 
@@ -353,6 +355,21 @@ smc_status smc_exp(const double *x, double *y, long long n);
  * arguments or host pointers. */
 smc_status smc_react_integrate(smc_handle *h, const double *U, const double *G, double dt,
                                double *Uout);
+
+/* Measured throughput of one fused multiply-add pipe of the current device:
+ * the denominator of the arithmetic rooflines (Sec. 2.3 counts the flops of
+ * the stencils; this measures the rate they can run at on this GPU).
+ *   kind 0: FP64 FMA (DFMA); 1: FP32 FMA; 2: paired FP32 FMA (two per lane
+ *   and instruction).
+ * One untimed launch, then one launch of multiProcessorCount x 4 blocks of
+ * 256 threads, each thread running 8 independent FMA chains for `iters`
+ * iterations, timed with CUDA events on a private stream.  *flops_per_s
+ * receives 2 x FMAs / s (required), *ms the timed launch's duration and
+ * *sm_count the device's SM count (both may be NULL).  Allocates and frees
+ * one small device buffer and synchronises.  SMC_ERR_ARG for kind outside
+ * 0..2 or iters outside 1..2^40, SMC_ERR_OOM, SMC_ERR_CUDA. */
+smc_status smc_fma_throughput(int kind, long long iters, double *flops_per_s, double *ms,
+                              int *sm_count);
 
 /* Message describing the last error on this handle ("" if none).  The
  * string is owned by the handle. */

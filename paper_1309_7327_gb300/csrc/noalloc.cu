@@ -1,20 +1,24 @@
 // smc_rhs_noalloc: the FP64 right-hand side of one periodic box without any
 // device allocation (see include/smc.h).
 //
-// Some callers cannot call cudaMalloc: code that runs inside CUDA stream
-// capture (where cudaMalloc/cudaFree are not permitted), applications whose
-// framework owns every byte of device memory in a fixed arena, and loops that
-// must not pay the implicit device synchronisation of cudaMalloc/cudaFree.
-// This entry point runs the same kernels as smc_rhs, but every scratch
-// array, table and constant lives in one file-scope static device array of
-// fixed size (kScratchBytes), reserved on every device that loads the
-// library until the process exits.
+// Some callers cannot call cudaMalloc: applications whose framework owns
+// every byte of device memory in a fixed arena (a cudaMalloc outside it
+// fails or breaks the arena's accounting), and loops that must not pay the
+// implicit device synchronisation of cudaMalloc/cudaFree.  This entry point
+// runs the same kernels as smc_rhs, but every scratch array, table and
+// constant lives in one file-scope static device array of fixed size
+// (kScratchBytes), reserved on every device that loads the library until the
+// process exits.
+//
+// The call copies its tables from host memory and waits for its stream
+// before it returns (it reads the evaluation's device status back), so it
+// must not be issued while that stream is being captured into a CUDA graph.
 //
 // The first call on a device looks up the array's device address with
-// cudaGetSymbolAddress (with that device current); make that first call
-// before any stream capture.  Calls share the array and it keeps the last
-// call's contents: calls that overlap on the GPU (different streams, or
-// different host threads) race and must be serialised by the caller.
+// cudaGetSymbolAddress (with that device current).  Calls share the array and
+// it keeps the last call's contents: calls that overlap on the GPU
+// (different streams, or different host threads) race and must be
+// serialised by the caller.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -29,6 +33,9 @@ using namespace smc;
 constexpr size_t kScratchBytes = 20u << 20;   // 20 MiB
 constexpr int kMaxDevices = 64;
 constexpr int kMaxReactions = 256;
+// no box side above this can fit the scratch (its ghost-cell map alone is
+// 4 (n + 8) 9 9 bytes); checked before any size product is formed
+constexpr int kMaxSide = 1 << 16;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
@@ -60,7 +67,23 @@ extern "C" smc_status smc_rhs_noalloc(const int n[3], const double dx[3],
                                       void *stream) {
   if (!n || !dx || !mech || !U || !dUdt) return SMC_ERR_ARG;
   for (int d = 0; d < 3; ++d)
-    if (n[d] < 1 || !(dx[d] > 0)) return SMC_ERR_ARG;
+    if (n[d] < 1 || n[d] > kMaxSide || !(dx[d] > 0)) return SMC_ERR_ARG;
+  // U and dUdt must be device memory of the current device (no staging: a
+  // host array would need a device buffer)
+  {
+    int cur = -1;
+    if (cudaGetDevice(&cur) != cudaSuccess) return SMC_ERR_CUDA;
+    const void *ptrs[2] = {U, dUdt};
+    for (const void *p : ptrs) {
+      cudaPointerAttributes a;
+      if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return SMC_ERR_ARG;
+      }
+      if (a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged) return SMC_ERR_ARG;
+      if (a.type == cudaMemoryTypeDevice && a.device != cur) return SMC_ERR_ARG;
+    }
+  }
   cudaStream_t st = (cudaStream_t)stream;
   const int ns = mech->nspecies;
   if (ns < 1 || ns > SMC_MAX_NS) return SMC_ERR_ARG;

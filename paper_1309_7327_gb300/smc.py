@@ -34,7 +34,8 @@ KERNELS = ["prim", "grad", "march", "final", "update", "fine", "chem", "other", 
 EXPORTS = ["smc_create", "smc_destroy", "smc_rhs", "smc_sdc_step", "smc_prim_to_cons", "smc_autotune",
            "smc_set_stream", "smc_set_option", "smc_get_stats", "smc_synchronize",
            "smc_invalidate", "smc_collocation", "smc_multirate_collocation", "smc_rhs_noalloc",
-           "smc_exp", "smc_heat2d", "smc_react_integrate", "smc_last_error"]
+           "smc_exp", "smc_heat2d", "smc_react_integrate", "smc_fma_throughput",
+           "smc_last_error"]
 
 
 class smc_grid(C.Structure):
@@ -96,6 +97,8 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
     lib.smc_exp.restype = C.c_int
     lib.smc_rhs_noalloc.argtypes = [C.POINTER(C.c_int), C.POINTER(C.c_double),
                                     C.POINTER(smc_mechanism), vp, vp, vp]
+    lib.smc_fma_throughput.argtypes = [C.c_int, C.c_longlong, C.POINTER(C.c_double),
+                                       C.POINTER(C.c_double), C.POINTER(C.c_int)]
     lib.smc_last_error.argtypes = [vp]
     lib.smc_last_error.restype = C.c_char_p
     for name in EXPORTS:
@@ -186,10 +189,20 @@ def smc_exp(x, y):
     return y
 
 
-def smc_rhs_noalloc(n, dx, mech, U, dUdt, stream=None):
-    """The allocation-free right-hand side of one periodic box (see smc.h).
-    n, dx: 3-sequences; mech: a synth.Mechanism-like object; U, dUdt: CUDA
-    tensors in the box layout."""
+def smc_fma_throughput(kind: int, iters: int):
+    """Measured FMA-pipe throughput of the current device (kind 0 FP64, 1 FP32,
+    2 paired FP32): returns (flop/s, ms of the timed launch, SM count)."""
+    fl, ms, sms = C.c_double(), C.c_double(), C.c_int()
+    st = lib().smc_fma_throughput(int(kind), C.c_longlong(int(iters)), C.byref(fl), C.byref(ms),
+                                  C.byref(sms))
+    if st != SMC_OK:
+        raise SmcError(st, "smc_fma_throughput")
+    return fl.value, ms.value, sms.value
+
+
+def mechanism_struct(mech):
+    """(smc_mechanism, keep-alive list) for a synth.Mechanism-like object;
+    the struct points into the arrays of the list."""
     keep = []
 
     def arr(a, t):
@@ -204,14 +217,28 @@ def smc_rhs_noalloc(n, dx, mech, U, dUdt, stream=None):
     m.A, m.b, m.Ea, m.Le = (arr(mech.A, np.float64), arr(mech.b, np.float64),
                             arr(mech.Ea, np.float64), arr(mech.Le, np.float64))
     m.eta_ref, m.T_ref, m.eta_exp, m.Pr = mech.eta_ref, mech.T_ref, mech.eta_exp, mech.Pr
+    return m, keep
+
+
+def smc_rhs_noalloc(n, dx, mech, U, dUdt, stream=None):
+    """The allocation-free right-hand side of one periodic box (see smc.h).
+    n, dx: 3-sequences; mech: a synth.Mechanism-like object; U, dUdt: CUDA
+    tensors in the box layout, on one device."""
+    m, keep = mechanism_struct(mech)
     nn = (C.c_int * 3)(*[int(v) for v in n])
     dd = (C.c_double * 3)(*[float(v) for v in dx])
     raw = getattr(stream, "cuda_stream", stream)
     need = (5 + mech.ns) * int(n[0]) * int(n[1]) * int(n[2])
-    for arr in (U, dUdt):
-        if arr.numel() != need:
-            raise ValueError(f"expected {need} values, got {arr.numel()}")
-    st = lib().smc_rhs_noalloc(nn, dd, C.byref(m), _ptr(U), _ptr(dUdt), C.c_void_p(raw))
+    for a in (U, dUdt):
+        if not getattr(a, "is_cuda", False):
+            raise ValueError("U and dUdt must be CUDA tensors (the call stages nothing)")
+        if a.device != U.device:
+            raise ValueError("U and dUdt must be on the same device")
+        if a.numel() != need:
+            raise ValueError(f"expected {need} values, got {a.numel()}")
+    import torch
+    with torch.cuda.device(U.device):
+        st = lib().smc_rhs_noalloc(nn, dd, C.byref(m), _ptr(U), _ptr(dUdt), C.c_void_p(raw))
     if st != SMC_OK:
         raise SmcError(st, "smc_rhs_noalloc")
     return dUdt
