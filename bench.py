@@ -57,7 +57,8 @@ def parse():
                     help="smaller instance of the workload (profiling captures)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
     ap.add_argument("--tiles", default=None,
-                    help="segment,x_layout,march: use this stencil schedule instead of autotuning")
+                    help="segment,x_layout,march[,persistent]: use this stencil schedule instead "
+                         "of autotuning")
     ap.add_argument("--fine-repeat", type=int, default=1,
                     help="multirate fine-node groups per coarse interval (1: type (b), >1: type (c))")
     ap.add_argument("--sdc-exit", type=float, default=0.0,
@@ -554,11 +555,15 @@ def main():
 
         rhs_default = rhs_ms()                # the library's default schedule
         if args.tiles:                        # a fixed schedule (profiling runs)
-            seg, xl, mv = (int(v) for v in args.tiles.split(","))
+            seg, xl, mv, *pers = (int(v) for v in args.tiles.split(","))
+            pers = pers[0] if pers else 0
+            if precision == 0 and mv == 3:
+                mv = 1
             h.set_option("segment", seg)
             h.set_option("x_layout", xl)
-            h.set_option("march", mv if precision == 1 else 0)
-            tuned = {"segment": seg, "x_layout": xl, "march": mv if precision == 1 else 0}
+            h.set_option("march", mv)
+            h.set_option("persistent", pers)
+            tuned = {"segment": seg, "x_layout": xl, "march": mv, "persistent": pers}
         else:
             tuned = h.autotune(U)             # segment length, x-line layout, line kernel
         tuned = dict(tuned, rhs_ms_default=rhs_default, rhs_ms_tuned=rhs_ms())
@@ -748,7 +753,9 @@ def main():
     torch.cuda.empty_cache()                  # the measured runs' tensors
     h2 = smc.Smc(wl.grid, wl.mech, dict(main_opts, segment=R["tuned"]["segment"],
                                         x_layout=R["tuned"]["x_layout"],
-                                        march=R["tuned"]["march"]), x_outflow=wl.x_outflow)
+                                        march=R["tuned"]["march"],
+                                        persistent=R["tuned"]["persistent"]),
+                 x_outflow=wl.x_outflow)
     h2.sdc_step(Uh, wl.dt, nodes, sweeps, rsub)
     e2e_steps = max(1, min(args.steps, 3))
     t0 = time.perf_counter()

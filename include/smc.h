@@ -134,12 +134,12 @@ enum {
   SMC_OPT_X_LAYOUT = 13,       /* x-direction lines of the current precision: 0 (default) read
                                   the box layout, 1 read an x-slowest copy made once per
                                   evaluation (nQ + 9 more ghosted planes of device memory) */
-  SMC_OPT_MARCH = 14,          /* stencil-line kernel of the current precision: 0 evaluates
-                                  every face from its 8-point window; 1, 2, 3 slide 9-cell
-                                  register windows along the line, one load per field and
-                                  cell, in chunks of 16 / 32 / 16 cells sized for 3 / 3 / 4
-                                  resident blocks per SM (mixed only; default 0 FP64,
-                                  1 mixed) */
+  SMC_OPT_MARCH = 14,          /* stencil-line kernel of the current precision.  FP64: 0 (default)
+                                  evaluates every face from its 8-point window; 1, 2 slide
+                                  9-cell register windows along the line, one load per field
+                                  and cell, in chunks of 16 / 32 cells.  Mixed: 1, 2, 3 slide
+                                  windows in chunks of 16 / 32 / 16 cells sized for 3 / 3 / 4
+                                  resident blocks per SM (0 is taken as 1; default 1) */
   SMC_OPT_RATES = 15,          /* production rates under SMC_OPT_PRECISION = 1: 0 (default)
                                   FP64 like the FP64 path; 1 FP32 mantissas after FP64 Gibbs
                                   energies, reaction exponents and exponent reductions
@@ -167,9 +167,15 @@ enum {
                                   at most 32 species) */
   SMC_OPT_BDF_RTOL = 20,       /* relative tolerance of the implicit reaction integration,
                                   0 < rtol < 1, default 1e-8 */
-  SMC_OPT_BDF_ATOL = 21        /* absolute tolerance of the implicit reaction integration in
+  SMC_OPT_BDF_ATOL = 21,       /* absolute tolerance of the implicit reaction integration in
                                   mass-fraction units (the weight of rho Y_k is
                                   atol rho + rtol |rho Y_k|), >= 0, default 1e-12 */
+  SMC_OPT_PERSISTENT = 22      /* launch shape of the multirate reaction chain and the
+                                  sliding-window line kernels: 0 (default) one thread per cell
+                                  or line segment, as many blocks as that takes; 1 one grid of
+                                  the device's resident capacity (blocks per SM from the
+                                  occupancy calculator x SM count) whose threads loop over the
+                                  work items, so no partly filled last wave of blocks */
 };
 
 /* Kernel classes counted in smc_stats (launches always; times only while
@@ -208,6 +214,10 @@ typedef struct {
   long long bdf_newton_failures;   /* attempts whose Newton iteration failed */
   long long bdf_evals;       /* production-rate evaluations */
   long long bdf_max_steps;   /* most accepted steps of one cell in one call */
+  int schedule[4];           /* the schedule in use for the current precision: segment
+                                length, x-line layout, line kernel (SMC_OPT_SEGMENT,
+                                SMC_OPT_X_LAYOUT, SMC_OPT_MARCH) and launch shape
+                                (SMC_OPT_PERSISTENT) */
 } smc_stats;
 
 /* Create a handle: validates the mechanism (limits above) and the grid,
@@ -271,7 +281,8 @@ smc_status smc_invalidate(smc_handle *h);
  * segment length (cells per thread along a stencil line: 8, 16, 32, 64),
  * both layouts of the x-direction lines (0: read the box layout directly;
  * 1: read a copy with x the slowest index, made once per evaluation) and
- * every stencil-line kernel of the precision (SMC_OPT_MARCH), and keep the
+ * every stencil-line kernel of the precision (SMC_OPT_MARCH), then the
+ * winner with the other launch shape (SMC_OPT_PERSISTENT), and keep the
  * fastest.  *segment, *x_layout and *march (each may be NULL) receive the
  * choice.  Synchronises the handle's stream. */
 smc_status smc_autotune(smc_handle *h, const double *U, int *segment, int *x_layout, int *march);

@@ -364,9 +364,10 @@ smc_status eval_rhs(smc_handle *h, const double *U, double *F, int transport, in
     for (int d = 0; d < 3; ++d) {
       {
         Timed t(h, SMC_K_MARCH);
-        if (mixed && h->march[1])
+        if (mixed)
           launch_march_m2(d == 0 ? sx : s, d, h->d_dUf, d == 0, h->march[1], h->stream);
-        else if (mixed) launch_march_m(d == 0 ? sx : s, d, h->d_dUf, d == 0, h->stream);
+        else if (h->march[0])
+          launch_march_w(d == 0 ? sx : s, d, F, d == 0, h->march[0], h->stream);
         else launch_march(d == 0 ? sx : s, d, F, d == 0, h->stream);
       }
       if (d == 0 && h->x_outflow && !h->hbc.empty()) {
@@ -998,6 +999,7 @@ smc_status smc_create(const smc_grid *grid, const smc_mechanism *mech, const smc
   h->opt.T0 = 1000.0;
   h->opt.xi_ratio = 0.0;
   h->opt.chain_blocks = 0;
+  h->opt.persistent = 0;
   build_coef(h);
   cudaGetDevice(&h->device);
   // ---- device memory
@@ -1291,8 +1293,8 @@ smc_status smc_set_option(smc_handle *h, int key, double v) {
       return SMC_OK;
     case SMC_OPT_MARCH:
       if (v < 0 || v > 3 || v != floor(v)) return fail(h, SMC_ERR_ARG, "march kernel must be 0..3");
-      if (v != 0.0 && h->precision != 1)
-        return fail(h, SMC_ERR_ARG, "the sliding-window line kernels are mixed precision only");
+      if (v == 3.0 && h->precision != 1)
+        return fail(h, SMC_ERR_ARG, "FP64 line kernels are 0..2");
       h->march[h->precision == 1] = (int)v;
       return SMC_OK;
     case SMC_OPT_FINE_REPEAT:
@@ -1302,6 +1304,10 @@ smc_status smc_set_option(smc_handle *h, int key, double v) {
     case SMC_OPT_CHAIN_BLOCKS:
       if (v < 0 || v > 16 || v != floor(v)) return fail(h, SMC_ERR_ARG, "chain blocks must be 0..16");
       h->opt.chain_blocks = (int)v;
+      return SMC_OK;
+    case SMC_OPT_PERSISTENT:
+      if (v != 0.0 && v != 1.0) return fail(h, SMC_ERR_ARG, "persistent must be 0 or 1");
+      h->opt.persistent = (int)v;
       return SMC_OK;
     case SMC_OPT_SDC_EXIT:
       if (!(v >= 0.0) || !std::isfinite(v)) return fail(h, SMC_ERR_ARG, "sdc exit must be >= 0");
@@ -1368,6 +1374,11 @@ smc_status smc_get_stats(smc_handle *h, smc_stats *o) {
   o->bdf_newton_failures = (long long)c[2];
   o->bdf_evals = (long long)c[3];
   o->bdf_max_steps = (long long)c[4];
+  const int mixed = h->precision == 1;
+  o->schedule[0] = h->segment;
+  o->schedule[1] = h->xt[mixed];
+  o->schedule[2] = h->march[mixed];
+  o->schedule[3] = h->opt.persistent;
   return SMC_OK;
 }
 
@@ -1392,7 +1403,7 @@ smc_status smc_autotune(smc_handle *h, const double *U, int *segment, int *x_lay
   h->cache_kind = 0;   // slot 0 is overwritten
   const int mixed = h->precision == 1;
   const int segs[4] = {8, 16, 32, 64};
-  const int nvar = mixed ? 4 : 1;
+  const int mv0 = mixed ? 1 : 0, nvar = mixed ? 4 : 3;   // mixed: the sliding-window kernels
   float best = 1e30f;
   int best_seg = h->segment, best_xt = h->xt[mixed], best_mv = h->march[mixed];
   cudaEvent_t a, b;
@@ -1407,7 +1418,7 @@ smc_status smc_autotune(smc_handle *h, const double *U, int *segment, int *x_lay
     if (cudaMemGetInfo(&fr, &tot) != cudaSuccess || fr < need + (need >> 2) + (1ull << 30))
       nx_layouts = 1;
   }
-  for (int mv = 0; mv < nvar; ++mv)
+  for (int mv = mv0; mv < nvar; ++mv)
     for (int si = 0; si < 4; ++si)
       for (int x = 0; x < nx_layouts; ++x) {
         h->segment = segs[si];
@@ -1429,6 +1440,26 @@ smc_status smc_autotune(smc_handle *h, const double *U, int *segment, int *x_lay
           best_mv = mv;
         }
       }
+  // the winner again with the other launch shape (resident-capacity grid or
+  // one thread per segment)
+  int best_pers = h->opt.persistent;
+  if (best_mv != 0 || mixed) {
+    h->segment = best_seg;
+    h->xt[mixed] = best_xt;
+    h->march[mixed] = best_mv;
+    h->opt.persistent = !best_pers;
+    if ((st = build_lines(h))) return st;
+    if ((st = eval_rhs(h, U, F, 1, 1))) return st;
+    CUDA_TRY(h, cudaEventRecord(a, h->stream));
+    for (int r = 0; r < 2; ++r)
+      if ((st = eval_rhs(h, U, F, 1, 1))) return st;
+    CUDA_TRY(h, cudaEventRecord(b, h->stream));
+    CUDA_TRY(h, cudaEventSynchronize(b));
+    float ms = 0.f;
+    CUDA_TRY(h, cudaEventElapsedTime(&ms, a, b));
+    if (ms < best) best_pers = !best_pers;
+  }
+  h->opt.persistent = best_pers;
   cudaEventDestroy(a);
   cudaEventDestroy(b);
   h->segment = best_seg;

@@ -45,6 +45,13 @@ __device__ __forceinline__ void put_pair(float *Qf, size_t NG, int plane, long l
   Qf[(size_t)(plane + 1) * NG + g] = lo;
 }
 
+// x rounded to the nearest float (ties away from zero) in integer
+// arithmetic: half a float ulp added to the magnitude, then truncated.
+// For finite x in the float range.
+__device__ __forceinline__ float round_float(double x) {
+  return trunc_float(__longlong_as_double(__double_as_longlong(x) + (1LL << 28)));
+}
+
 __device__ __forceinline__ f2 get_pair(const float *__restrict__ Qf, size_t NG, int plane,
                                        long long g) {
   f2 r;
@@ -98,7 +105,6 @@ __global__ void __launch_bounds__(128) k_prim_m(const DevState s, const double *
     if (flag) atomicOr(s.status, flag);
 
     double wmix = 0.0;
-    const float cpm = trunc_float(cpd);
     const float Tf = trunc_float(T);
     float h32[SMC_MAX_NS];
     for (int k = 0; k < ns; ++k) {
@@ -109,13 +115,18 @@ __global__ void __launch_bounds__(128) k_prim_m(const DevState s, const double *
       h32[k] = m.Ru_Wf[k] * hRf;
     }
     const double p = rho * kRu * T * wmix;
-    const float invp = 1.0f / trunc_float(p);
     const double inv_wmix = 1.0 / wmix;
-    // transport in FP32
-    const float eta = m.eta_ref_f * __powf(Tf * m.inv_T_ref_f, m.eta_exp_f);
-    const float xi = s.xi_ratio_f * eta;
-    const float lam = cpm * eta * m.inv_Pr_f;
-    const float rd0 = lam / cpm;
+    // Transport coefficients: computed in FP64 from the FP64 temperature and
+    // rounded once to float.  They multiply stencil products whose face sums
+    // cancel (a species' gradient and pressure fluxes can be several times its
+    // net flux, and a face flux tens of times its divergence), so rounding
+    // noise from a chain of FP32 operations would be amplified by as much.
+    const double eta_d = m.eta_ref * fast_exp(m, m.eta_exp * log(T * m.inv_T_ref));
+    const double xi_d = s.opt.xi_ratio * eta_d;
+    const double rd0_d = eta_d * m.inv_Pr;           // lambda / cp = rho D_k Le_k
+    const double bq = rd0_d / p;                     // B_k = bq (X_k - Y_k) / Le_k
+    const float eta = round_float(eta_d);
+    const float lam = round_float(cpd * rd0_d);
     put_pair(Qf, NG, PM_U, g, u);
     put_pair(Qf, NG, PM_V, g, v);
     put_pair(Qf, NG, PM_W, g, w);
@@ -127,20 +138,22 @@ __global__ void __launch_bounds__(128) k_prim_m(const DevState s, const double *
     put_pair(Qf, NG, PM_HMIX, g, hm);
     put_pair(Qf, NG, PM_RHO, g, rho);
     put_pair(Qf, NG, PM_RHOH, g, rhoE + p);
-    Qf[(size_t)PM_C43 * NG + g] = 4.0f / 3.0f * eta + xi;
+    Qf[(size_t)PM_C43 * NG + g] = round_float(4.0 / 3.0 * eta_d + xi_d);
     Qf[(size_t)PM_ETA * NG + g] = eta;
-    Qf[(size_t)PM_C23 * NG + g] = xi - 2.0f / 3.0f * eta;
+    Qf[(size_t)PM_C23 * NG + g] = round_float(xi_d - 2.0 / 3.0 * eta_d);
     Qf[(size_t)PM_LAM * NG + g] = lam;
     const float href = (mode == 1) ? h32[ref] : 0.0f;
-    float ap = 0.0f, sb = 0.0f;
+    float ap = 0.0f;
+    double sb = 0.0;                                 // sum_k B_k: its terms cancel (sum X = sum Y)
     for (int k = 0; k < ns; ++k) {
       const double X = Y[k] * m.invW[k] * inv_wmix;
-      const float rd = rd0 * m.invLef[k];
-      const float B = rd * trunc_float(X - Y[k]) * invp;
+      const float rd = round_float(rd0_d * m.invLe[k]);
+      const double Bd = bq * m.invLe[k] * (X - Y[k]);
+      const float B = round_float(Bd);
       const float hp = h32[k] - href;
       if (mode == 0) {
         ap += h32[k] * B;
-        sb += B;
+        sb += Bd;
       } else if (k != ref) {
         ap += hp * B;
       }
@@ -152,7 +165,7 @@ __global__ void __launch_bounds__(128) k_prim_m(const DevState s, const double *
       Qf[(size_t)pmB(ns, k) * NG + g] = B;
     }
     Qf[(size_t)PM_AP * NG + g] = ap;
-    Qf[(size_t)PM_SB * NG + g] = sb;
+    Qf[(size_t)PM_SB * NG + g] = round_float(sb);
   }
 }
 
@@ -214,223 +227,12 @@ __global__ void __launch_bounds__(128) k_grad_m(const DevState s, const GradPara
   }
 }
 
-// ------------------------------------------------------------ k_march_m
+// ------------------------------------------------------------ line-kernel constants
 struct MarchParamsM {
   float M[8][8];
   float D[4];
   float2 MT2[8][4];               // (M[2j][t], M[2j+1][t]): two rows of a column, for FFMA2
 };
-
-// w[m] = sum_{n != 3} M[m][n] (x_n - x_3) for a window of float pairs
-__device__ __forceinline__ void mv_pair(const MarchParamsM &P, const float *__restrict__ Qf,
-                                        size_t NG, int plane, long long gw, int sg, float *w) {
-  float d[8];
-  const f2 x3 = get_pair(Qf, NG, plane, gw + 3 * sg);
-#pragma unroll
-  for (int t = 0; t < 8; ++t) d[t] = (t == 3) ? 0.0f : diff(get_pair(Qf, NG, plane, gw + t * sg), x3);
-#pragma unroll
-  for (int mm = 0; mm < 8; ++mm) {
-    float acc = 0.0f;
-#pragma unroll
-    for (int t = 0; t < 8; ++t)
-      if (t != 3 && mm - t <= 4 && t - mm <= 4) acc = fmaf(P.M[mm][t], d[t], acc);
-    w[mm] = acc;
-  }
-}
-
-// v[n] = sum_m a_m M[m][n] (n != 3) for a window of floats
-__device__ __forceinline__ void vm_single(const MarchParamsM &P, const float *__restrict__ Qf,
-                                          size_t NG, int plane, long long gw, int sg, float *v) {
-  float a[8];
-#pragma unroll
-  for (int t = 0; t < 8; ++t) a[t] = __ldg(Qf + (size_t)plane * NG + gw + t * sg);
-#pragma unroll
-  for (int n = 0; n < 8; ++n) {
-    float acc = 0.0f;
-#pragma unroll
-    for (int mm = 0; mm < 8; ++mm)
-      if (n != 3 && mm - n <= 4 && n - mm <= 4) acc = fmaf(a[mm], P.M[mm][n], acc);
-    v[n] = acc;
-  }
-}
-
-// sum_{n != 3} v_n (x_n - x_3) for a window of float pairs
-__device__ __forceinline__ float dot_pair(const float *v, const float *__restrict__ Qf, size_t NG,
-                                          int plane, long long gw, int sg) {
-  const f2 x3 = get_pair(Qf, NG, plane, gw + 3 * sg);
-  float acc = 0.0f;
-#pragma unroll
-  for (int t = 0; t < 8; ++t)
-    if (t != 3) acc = fmaf(v[t], diff(get_pair(Qf, NG, plane, gw + t * sg), x3), acc);
-  return acc;
-}
-
-// sum_m a_m w_m for a window of floats
-__device__ __forceinline__ float dot_single(const float *w, const float *__restrict__ Qf, size_t NG,
-                                            int plane, long long gw, int sg) {
-  float acc = 0.0f;
-#pragma unroll
-  for (int t = 0; t < 8; ++t) acc = fmaf(__ldg(Qf + (size_t)plane * NG + gw + t * sg), w[t], acc);
-  return acc;
-}
-
-template <int DIR>
-__device__ __forceinline__ void face_fluxes_m(const DevState &s, const MarchParamsM &P, long long gw,
-                                              int sg, float *H) {
-  constexpr int E = (DIR + 1) % 3, F = (DIR + 2) % 3;
-  const size_t NG = (size_t)s.nghost;
-  const float *__restrict__ Qf = reinterpret_cast<const float *>(s.Q);
-  const int ns = s.ns, mode = s.opt.mode, ref = s.opt.ref;
-  float wp[8], vA[8], vB[8], wk[8];
-  mv_pair(P, Qf, NG, PM_P, gw, sg, wp);
-  vm_single(P, Qf, NG, PM_C43, gw, sg, vA);
-  vm_single(P, Qf, NG, PM_ETA, gw, sg, vB);
-  H[0] = dot_pair(vA, Qf, NG, PM_U + 2 * DIR, gw, sg);
-  H[1] = dot_pair(vB, Qf, NG, PM_U + 2 * E, gw, sg);
-  H[2] = dot_pair(vB, Qf, NG, PM_U + 2 * F, gw, sg);
-  float HE = dot_pair(vA, Qf, NG, PM_KX + 2 * DIR, gw, sg);
-  HE += dot_pair(vB, Qf, NG, PM_KX + 2 * E, gw, sg);
-  HE += dot_pair(vB, Qf, NG, PM_KX + 2 * F, gw, sg);
-  mv_pair(P, Qf, NG, PM_T, gw, sg, wk);
-  HE += dot_single(wk, Qf, NG, PM_LAM, gw, sg);
-  HE += dot_single(wp, Qf, NG, PM_AP, gw, sg);
-  for (int k = 0; k < ns; ++k) {
-    if (mode == 1 && k == ref) {
-      H[4 + k] = 0.0f;
-      continue;
-    }
-    mv_pair(P, Qf, NG, pmX(ns, k), gw, sg, wk);
-    H[4 + k] = dot_single(wk, Qf, NG, pmRD(ns, k), gw, sg) + dot_single(wp, Qf, NG, pmB(ns, k), gw, sg);
-    HE += dot_single(wk, Qf, NG, pmRDH(ns, k), gw, sg);
-  }
-  H[3] = HE;
-}
-
-template <int DIR>
-__global__ void __launch_bounds__(128, 4) k_march_m(const DevState s, const MarchParamsM P,
-                                                    float *__restrict__ dUf, int first) {
-  const long long item = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (item >= s.nlines[DIR]) return;
-  const LineItem L = s.lines[DIR][item];
-  constexpr int E = (DIR + 1) % 3, F = (DIR + 2) % 3;
-  const int ns = s.ns, nv = s.nv, mode = s.opt.mode, ref = s.opt.ref;
-  const size_t NG = (size_t)s.nghost, NI = (size_t)s.ncells;
-  const float *__restrict__ Qf = reinterpret_cast<const float *>(s.Q);
-  const float *__restrict__ Gf = reinterpret_cast<const float *>(s.G);
-  float *__restrict__ divf = reinterpret_cast<float *>(s.divacc);
-  const int sg = L.sg;
-
-  float Hp[4 + SMC_MAX_NS], Hn[4 + SMC_MAX_NS], out[5 + SMC_MAX_NS];
-  face_fluxes_m<DIR>(s, P, L.g0 - 4LL * sg, sg, Hp);
-  for (int c = 0; c < L.len; ++c) {
-    const long long gc = L.g0 + (long long)c * sg;
-    const long long ic = L.i0 + (long long)c * L.si;
-    face_fluxes_m<DIR>(s, P, gc - 3LL * sg, sg, Hn);
-    out[0] = 0.0f;
-    out[1 + DIR] = Hn[0] - Hp[0];
-    out[1 + E] = Hn[1] - Hp[1];
-    out[1 + F] = Hn[2] - Hp[2];
-    out[4] = Hn[3] - Hp[3];
-    float sumN = 0.0f;
-    for (int k = 0; k < ns; ++k) {
-      const float N = Hn[4 + k] - Hp[4 + k];
-      out[5 + k] = N;
-      sumN += N;
-    }
-    if (mode == 1) out[5 + ref] = -sumN;
-
-    // -D_d of the convective fluxes (float-pair products) and mixed viscous terms
-    float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f, a4 = 0.f;
-    f2 udp[4], udm[4];
-#pragma unroll
-    for (int n = 1; n <= 4; ++n) {
-      f2 fl[2][5];
-      float vis[2][3];
-#pragma unroll
-      for (int side = 0; side < 2; ++side) {
-        const long long j = side == 0 ? gc + n * sg : gc - n * sg;
-        const f2 rho = get_pair(Qf, NG, PM_RHO, j), ud = get_pair(Qf, NG, PM_U + 2 * DIR, j);
-        const f2 ue = get_pair(Qf, NG, PM_U + 2 * E, j), uf = get_pair(Qf, NG, PM_U + 2 * F, j);
-        const f2 rH = get_pair(Qf, NG, PM_RHOH, j);
-        const float c23 = __ldg(Qf + (size_t)PM_C23 * NG + j), eta = __ldg(Qf + (size_t)PM_ETA * NG + j);
-        const float Gee = __ldg(Gf + (size_t)(3 * E + E) * NG + j);
-        const float Gff = __ldg(Gf + (size_t)(3 * F + F) * NG + j);
-        const float Ged = __ldg(Gf + (size_t)(3 * E + DIR) * NG + j);
-        const float Gfd = __ldg(Gf + (size_t)(3 * F + DIR) * NG + j);
-        const float tdiv = c23 * (Gee + Gff);
-        const f2 mass = mul(rho, ud);
-        fl[side][0] = mass;
-        fl[side][1] = mul(mass, ud);
-        fl[side][2] = mul(mass, ue);
-        fl[side][3] = mul(mass, uf);
-        fl[side][4] = mul(rH, ud);
-        vis[side][0] = tdiv;
-        vis[side][1] = eta * Ged;
-        vis[side][2] = eta * Gfd;
-        // viscous work: tdiv u_d + eta (Ged u_e + Gfd u_f), plain floats
-        fl[side][4].l -= tdiv * (ud.h + ud.l) + eta * (Ged * (ue.h + ue.l) + Gfd * (uf.h + uf.l));
-        if (side == 0) udp[n - 1] = ud; else udm[n - 1] = ud;
-      }
-      const float dn = P.D[n - 1];
-      const f2 pp = get_pair(Qf, NG, PM_P, gc + n * sg), pm = get_pair(Qf, NG, PM_P, gc - n * sg);
-      a0 = fmaf(dn, diff(fl[0][0], fl[1][0]), a0);
-      a1 = fmaf(dn, diff(fl[0][1], fl[1][1]) + diff(pp, pm) - (vis[0][0] - vis[1][0]), a1);
-      a2 = fmaf(dn, diff(fl[0][2], fl[1][2]) - (vis[0][1] - vis[1][1]), a2);
-      a3 = fmaf(dn, diff(fl[0][3], fl[1][3]) - (vis[0][2] - vis[1][2]), a3);
-      a4 = fmaf(dn, diff(fl[0][4], fl[1][4]), a4);
-    }
-    out[0] -= a0;
-    out[1 + DIR] -= a1;
-    out[1 + E] -= a2;
-    out[1 + F] -= a3;
-    out[4] -= a4;
-    for (int k = 0; k < ns; ++k) {
-      float acc = 0.0f;
-#pragma unroll
-      for (int n = 1; n <= 4; ++n)
-        acc = fmaf(P.D[n - 1], diff(mul(get_pair(Qf, NG, pmRY(ns, k), gc + n * sg), udp[n - 1]),
-                                    mul(get_pair(Qf, NG, pmRY(ns, k), gc - n * sg), udm[n - 1])), acc);
-      out[5 + k] -= acc;
-    }
-
-    if (mode == 0) {
-      float Dp = 0.0f;
-#pragma unroll
-      for (int n = 1; n <= 4; ++n)
-        Dp = fmaf(P.D[n - 1], diff(get_pair(Qf, NG, PM_P, gc + n * sg), get_pair(Qf, NG, PM_P, gc - n * sg)), Dp);
-      float Vc = -__ldg(Qf + (size_t)PM_SB * NG + gc) * Dp;
-      for (int l = 0; l < ns; ++l) {
-        float DX = 0.0f;
-#pragma unroll
-        for (int n = 1; n <= 4; ++n)
-          DX = fmaf(P.D[n - 1], diff(get_pair(Qf, NG, pmX(ns, l), gc + n * sg),
-                                     get_pair(Qf, NG, pmX(ns, l), gc - n * sg)), DX);
-        Vc -= __ldg(Qf + (size_t)pmRD(ns, l) * NG + gc) * DX;
-      }
-      for (int k = 0; k < ns; ++k) {
-        float DY = 0.0f;
-#pragma unroll
-        for (int n = 1; n <= 4; ++n)
-          DY = fmaf(P.D[n - 1], diff(get_pair(Qf, NG, pmY(ns, k), gc + n * sg),
-                                     get_pair(Qf, NG, pmY(ns, k), gc - n * sg)), DY);
-        out[5 + k] += DY * Vc;
-      }
-      float Dh = 0.0f;
-#pragma unroll
-      for (int n = 1; n <= 4; ++n)
-        Dh = fmaf(P.D[n - 1], diff(get_pair(Qf, NG, PM_HMIX, gc + n * sg),
-                                   get_pair(Qf, NG, PM_HMIX, gc - n * sg)), Dh);
-      out[4] += Dh * Vc;
-      if (first) divf[ic] = sumN; else divf[ic] += sumN;
-    }
-    if (first) {
-      for (int c2 = 0; c2 < nv; ++c2) dUf[(size_t)c2 * NI + ic] = out[c2];
-    } else {
-      for (int c2 = 0; c2 < nv; ++c2) dUf[(size_t)c2 * NI + ic] += out[c2];
-    }
-    for (int x = 0; x < 4 + ns; ++x) Hp[x] = Hn[x];
-  }
-}
 
 // ------------------------------------------------------------ k_final_m
 // dUdt (FP64) = float stencil sum + correction terms (FP32) + rho omega_k (FP64)
@@ -502,19 +304,6 @@ void launch_grad_m(const DevState &s, cudaStream_t st) {
     for (int k = 0; k < 4; ++k) P.D[d][k] = (float)s.hcoef->D[d][k];
   P.ihx = s.hcoef->D[0][0] * 1.25;
   k_grad_m<<<grid_for(s.nghost, 128), 128, 0, st>>>(s, P);
-}
-
-void launch_march_m(const DevState &s, int dir, float *dUf, int first, cudaStream_t st) {
-  MarchParamsM P;
-  for (int a = 0; a < 8; ++a)
-    for (int b = 0; b < 8; ++b) P.M[a][b] = (float)s.hcoef->M[dir][a][b];
-  for (int k = 0; k < 4; ++k) P.D[k] = (float)s.hcoef->D[dir][k];
-  const long long n = s.nlines[dir];
-  if (n == 0) return;
-  const int blocks = (int)((n + 127) / 128);
-  if (dir == 0) k_march_m<0><<<blocks, 128, 0, st>>>(s, P, dUf, first);
-  else if (dir == 1) k_march_m<1><<<blocks, 128, 0, st>>>(s, P, dUf, first);
-  else k_march_m<2><<<blocks, 128, 0, st>>>(s, P, dUf, first);
 }
 
 void launch_final_m(const DevState &s, const double *U, const float *dUf, double *dU, int transport,
@@ -612,6 +401,67 @@ __device__ __forceinline__ void mv(const MarchParamsM &P, const f2 *x, int o, fl
     w[2 * j + 1] = acc[j].y;
   }
 }
+// w[m] = sum_{n != 3} M[m][n] d[n] for given differences d (d[3] unused)
+__device__ __forceinline__ void mvd(const MarchParamsM &P, const float *d, float *w) {
+  float2 acc[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) acc[j] = make_float2(0.0f, 0.0f);
+#pragma unroll
+  for (int t = 0; t < 8; ++t) {
+    if (t == 3) continue;
+    const float2 dd = make_float2(d[t], d[t]);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int m0 = 2 * j, m1 = 2 * j + 1;
+      const bool nz = (m0 - t <= 4 && t - m0 <= 4) || (m1 - t <= 4 && t - m1 <= 4);
+      if (nz) acc[j] = __ffma2_rn(P.MT2[t][j], dd, acc[j]);
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    w[2 * j] = acc[j].x;
+    w[2 * j + 1] = acc[j].y;
+  }
+}
+// For the 9-cell pair window x (cells c-4 .. c+4) the change, from the face
+// left of cell c (window cells 0..7) to the face right of it (1..8), of the
+// differences the narrow stencil multiplies: with d_f[n] = x[f+n] - x[f+3],
+//   dd[n] = d_1[n] - d_0[n] = (x[n+1] - x[n]) - (x[4] - x[3]),
+// formed from the pairs' neighbour differences (the high parts of neighbouring
+// values subtract exactly), so dd carries the second differences of x at
+// FP32 precision relative to themselves.
+__device__ __forceinline__ void ddiffs(const f2 *x, float *dd) {
+  const float d3h = x[4].h - x[3].h, d3l = x[4].l - x[3].l;
+#pragma unroll
+  for (int t = 0; t < 8; ++t) {
+    if (t == 3) {
+      dd[t] = 0.0f;
+    } else {
+      const float2 e = __fadd2_rn(make_float2(x[t + 1].h - x[t].h, x[t + 1].l - x[t].l),
+                                  make_float2(-d3h, -d3l));
+      dd[t] = e.x + e.y;
+    }
+  }
+}
+// The flux difference H_1 - H_0 of a narrow term between the faces right and
+// left of cell c, with H_f = sum_m a[f+m] w_f[m], formed directly:
+//   H_1 - H_0 = sum_m a[1+m] (w_1 - w_0)[m] + (a[1+m] - a[m]) w_0[m],
+// w_1 - w_0 = M dd (ddiffs).  Every product is of the size of the result,
+// instead of the face fluxes' (which can be tens of times larger and cancel),
+// so FP32 rounding is not amplified by that ratio.  w0: the left face's w.
+__device__ __forceinline__ float flux_diff(const MarchParamsM &P, const float *a, const f2 *x,
+                                           const float *w0) {
+  float dd[8], dw[8];
+  ddiffs(x, dd);
+  mvd(P, dd, dw);
+  float2 acc = make_float2(0.0f, 0.0f);
+#pragma unroll
+  for (int t = 0; t < 8; t += 2) {
+    acc = __ffma2_rn(make_float2(a[1 + t], a[2 + t]), make_float2(dw[t], dw[t + 1]), acc);
+    acc = __ffma2_rn(make_float2(a[1 + t] - a[t], a[2 + t] - a[1 + t]), make_float2(w0[t], w0[t + 1]), acc);
+  }
+  return acc.x + acc.y;
+}
 // sum_{n != 3} v[n] (x[o+n] - x[o+3])
 __device__ __forceinline__ float dp(const float *v, const f2 *x, int o) {
   float d[8];
@@ -697,14 +547,16 @@ __global__ void __launch_bounds__(M2_NT, MINB) k_march_m2(const DevState s, cons
   float(*sN)[M2_NT] = sV + CH;
   float(*sO)[M2_NT] = sN + CH;
   const int tid = threadIdx.x;
-  const long long item = blockIdx.x * (long long)blockDim.x + tid;
-  if (item >= s.nlines[DIR]) return;   // no block-wide barrier below
-  const LineItem L = s.lines[DIR][item];
   constexpr int E_ = (DIR + 1) % 3, F_ = (DIR + 2) % 3;
   const int ns = s.ns, mode = s.opt.mode, ref = s.opt.ref;
   const size_t NI = (size_t)s.ncells;
   float *__restrict__ divf = reinterpret_cast<float *>(s.divacc);
   const bool st = first != 0;
+  // one line segment per thread and iteration (a grid smaller than the
+  // segment count loops); no block-wide barrier below
+  for (long long item = blockIdx.x * (long long)blockDim.x + tid; item < s.nlines[DIR];
+       item += (long long)gridDim.x * blockDim.x) {
+  const LineItem L = s.lines[DIR][item];
   Win x;
   x.Qf = reinterpret_cast<const float *>(s.Q);
   x.Gf = reinterpret_cast<const float *>(s.G);
@@ -901,16 +753,16 @@ __global__ void __launch_bounds__(M2_NT, MINB) k_march_m2(const DevState s, cons
       }
       float w[8];
       mv(P, X, 0, w);
-      float H = ds(rd, 0, w), He = ds(rdh, 0, w);
+      float He = ds(rdh, 0, w);
 #pragma unroll 1
       for (int c = 0; c < n; ++c) {
         if (mode == 0) sV[c][tid] -= rd[4] * Dp(P, X);
+        const float N = flux_diff(P, rd, X, w);
         mv(P, X, 1, w);
-        const float H2 = ds(rd, 1, w), He2 = ds(rdh, 1, w);
-        put(dUf, NI, 5 + k, ib + (long long)c * L.si, H2 - H, st);
-        sN[c][tid] += H2 - H;
+        const float He2 = ds(rdh, 1, w);
+        put(dUf, NI, 5 + k, ib + (long long)c * L.si, N, st);
+        sN[c][tid] += N;
         sE[c][tid] += He2 - He;
-        H = H2;
         He = He2;
         if (c + 1 < n) {
           slide(X); slide(rd); slide(rdh);
@@ -936,17 +788,15 @@ __global__ void __launch_bounds__(M2_NT, MINB) k_march_m2(const DevState s, cons
       }
       float w[8];
       mv(P, p, 0, w);
-      float H = ds(B, 0, w);
 #pragma unroll 1
       for (int c = 0; c < n; ++c) {
         float o = -Dp(P, Fk);
         if (mode == 0) o = fmaf(Dp(P, Yk), sV[c][tid], o);
         if (narrow) {
+          const float N = flux_diff(P, B, p, w);
           mv(P, p, 1, w);
-          const float H2 = ds(B, 1, w);
-          o += H2 - H;
-          sN[c][tid] += H2 - H;
-          H = H2;
+          o += N;
+          sN[c][tid] += N;
         }
         put(dUf, NI, 5 + k, ib + (long long)c * L.si, o, false);
         if (c + 1 < n) {
@@ -984,6 +834,7 @@ __global__ void __launch_bounds__(M2_NT, MINB) k_march_m2(const DevState s, cons
     }
     for (int c = 0; c < n; ++c) put(dUf, NI, 4, ib + (long long)c * L.si, sE[c][tid], st);
   }
+  }
 }
 
 template <int CH, int MINB>
@@ -1000,6 +851,11 @@ static void launch_m2_variant(const DevState &s, int dir, const MarchParamsM &P,
     cudaFuncSetAttribute(k_march_m2<1, CH, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     cudaFuncSetAttribute(k_march_m2<2, CH, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     attr_set[dev] = true;
+  }
+  if (s.opt.persistent) {
+    static int cache[64] = {};
+    const int r = resident_blocks(k_march_m2<1, CH, MINB>, M2_NT, smem, cache);
+    if (blocks > r) blocks = r;
   }
   if (dir == 0) k_march_m2<0, CH, MINB><<<blocks, M2_NT, smem, st>>>(s, P, dUf, first);
   else if (dir == 1) k_march_m2<1, CH, MINB><<<blocks, M2_NT, smem, st>>>(s, P, dUf, first);

@@ -272,8 +272,18 @@ void launch_fine_chain(const DevState &s, const double *Uin, double *Uout, const
       attr_set[dev] = true;
     }
   }
-  if (s.opt.rates32) k_fine_chain<true><<<grid_for(s.ncells, 128), 128, smem, st>>>(s, Uin, Uout, fc);
-  else k_fine_chain<false><<<grid_for(s.ncells, 128), 128, smem, st>>>(s, Uin, Uout, fc);
+  int blocks = grid_for(s.ncells, 128);
+  if (s.opt.persistent) {
+    // the chain is a grid-stride loop: a grid of the resident capacity
+    // leaves no partly filled last wave
+    static int cache[2][64] = {};
+    const int r = s.opt.rates32 ? resident_blocks(k_fine_chain<true>, 128, smem, cache[1])
+                                : resident_blocks(k_fine_chain<false>, 128, smem, cache[0]);
+    const long long need = (s.ncells + 127) / 128;
+    blocks = (int)(need < r ? need : r);
+  }
+  if (s.opt.rates32) k_fine_chain<true><<<blocks, 128, smem, st>>>(s, Uin, Uout, fc);
+  else k_fine_chain<false><<<blocks, 128, smem, st>>>(s, Uin, Uout, fc);
 }
 
 }  // namespace smc

@@ -99,6 +99,7 @@ struct Opts {
   int maxit;
   int rates32;                    // 1: production rates with FP32 mantissas (mixed precision only)
   int chain_blocks;               // cap on resident reaction-chain blocks per SM (0: none)
+  int persistent;                 // 1: resident-capacity grids that loop over their work items
   double tol, T0, xi_ratio;
 };
 
@@ -179,9 +180,30 @@ struct DevState {
 void launch_xbc(const DevState &s, double *dU, cudaStream_t st);
 void launch_xbc_m(const DevState &s, float *dUf, cudaStream_t st);
 
+// Blocks of `threads` threads and `smem` bytes of dynamic shared memory that
+// the current device holds at once for kernel f (occupancy calculator x SM
+// count), cached per device in *cache (an array of 64, zero-initialised) on
+// the first (eager) launch, before any stream capture.
+template <typename K>
+int resident_blocks(K f, int threads, size_t smem, int *cache) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) return 152;
+  if (!cache[dev]) {
+    int sms = 0, per = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, f, threads, smem);
+    cache[dev] = per * sms > 0 ? per * sms : 1;
+  }
+  return cache[dev];
+}
+
 void launch_prim(const DevState &s, const double *U, cudaStream_t st);
 void launch_grad(const DevState &s, cudaStream_t st);
 void launch_march(const DevState &s, int dir, double *dUdt, int first, cudaStream_t st);
+// FP64 sliding-window line kernel (variant 1: 16-cell chunks, 2: 32-cell chunks)
+void launch_march_w(const DevState &s, int dir, double *dUdt, int first, int variant,
+                    cudaStream_t st);
 void launch_final(const DevState &s, double *dUdt, int transport, int chemistry, cudaStream_t st);
 void launch_prim_to_cons(const DevState &s, const double *prim, double *U, cudaStream_t st);
 // Copy `planes` planes of element size `esize` (4 or 8) from the box layout
@@ -194,7 +216,6 @@ void launch_transpose_x(const DevState &s, const void *src, void *dst, int plane
 int nQm(int ns);
 void launch_prim_m(const DevState &s, const double *U, cudaStream_t st);
 void launch_grad_m(const DevState &s, cudaStream_t st);
-void launch_march_m(const DevState &s, int dir, float *dUf, int first, cudaStream_t st);
 // variant 1: 16-cell chunks, 3 blocks/SM; 2: 32-cell chunks, 3 blocks/SM;
 // 3: 16-cell chunks, 4 blocks/SM
 void launch_march_m2(const DevState &s, int dir, float *dUf, int first, int variant,

@@ -28,7 +28,8 @@ STATUS_NAMES = {0: "SMC_OK", 1: "SMC_ERR_ARG", 2: "SMC_ERR_CUDA", 3: "SMC_ERR_OO
 OPT = dict(precision=0, m47=1, m48=2, diffusion_mode=3, ref_species=4, xi_ratio=5,
            newton_tol=6, newton_maxit=7, t_guess=8, reactions=9, segment=10, profile=11,
            use_graphs=12, x_layout=13, march=14, rates=15,
-           fine_repeat=16, sdc_exit=17, chain_blocks=18, mr_mode=19, bdf_rtol=20, bdf_atol=21)
+           fine_repeat=16, sdc_exit=17, chain_blocks=18, mr_mode=19, bdf_rtol=20, bdf_atol=21,
+           persistent=22)
 KERNELS = ["prim", "grad", "march", "final", "update", "fine", "chem", "other", "bdf"]
 
 EXPORTS = ["smc_create", "smc_destroy", "smc_rhs", "smc_sdc_step", "smc_prim_to_cons", "smc_autotune",
@@ -67,7 +68,8 @@ class smc_stats(C.Structure):
                 ("kernel_ms", C.c_double * 9), ("sweeps_done", C.c_int),
                 ("residual", C.c_double * 64), ("bdf_steps", C.c_longlong),
                 ("bdf_rejected", C.c_longlong), ("bdf_newton_failures", C.c_longlong),
-                ("bdf_evals", C.c_longlong), ("bdf_max_steps", C.c_longlong)]
+                ("bdf_evals", C.c_longlong), ("bdf_max_steps", C.c_longlong),
+                ("schedule", C.c_int * 4)]
 
 
 def load_library(path: str = LIB_PATH) -> C.CDLL:
@@ -368,7 +370,8 @@ class Smc:
         seg, xl, mv = C.c_int(), C.c_int(), C.c_int()
         self._check(lib().smc_autotune(self.h, self._state(U), C.byref(seg), C.byref(xl),
                                        C.byref(mv)))
-        return {"segment": seg.value, "x_layout": xl.value, "march": mv.value}
+        return {"segment": seg.value, "x_layout": xl.value, "march": mv.value,
+                "persistent": self.stats()["schedule"][3]}
 
     def synchronize(self):
         self._check(lib().smc_synchronize(self.h))
@@ -383,6 +386,7 @@ class Smc:
         out["launches"] = dict(zip(KERNELS, list(s.launches)))
         out["kernel_ms"] = dict(zip(KERNELS, list(s.kernel_ms)))
         out["residual"] = list(s.residual)[:max(s.sweeps_done, 0)]
+        out["schedule"] = list(s.schedule)
         return out
 
     def close(self):

@@ -148,3 +148,69 @@ def test_mixed_state_after_20_steps_of_the_flame(smc):
     print("mixed 20-step state error", np.array2string(state, precision=2))
     assert inc.max() < TOL_MIXED, inc
     assert state.max() < TOL_MIXED, state
+
+
+def _golden_c3():
+    """The oracle's state after 20 SDC steps of the flame configuration on a
+    64^3 box (tests/golden/c3_flame_n64_20steps.txt, written by
+    tests/golden/make_c3_flame_state.py from the oracle alone)."""
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "c3_flame_n64_20steps.txt")
+    cells, vals, inc_max, u_max = [], [], None, None
+    for line in open(path):
+        if line.startswith("inc_max "):
+            inc_max = np.array([float(v) for v in line.split()[1:]])
+        elif line.startswith("u_max "):
+            u_max = np.array([float(v) for v in line.split()[1:]])
+        elif line.startswith("cell "):
+            parts = line.split()
+            cells.append(tuple(int(v) for v in parts[1:4]))
+            vals.append([float(v) for v in parts[4:]])
+    return cells, np.array(vals).T, inc_max, u_max
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_flame_state_after_20_steps_on_64_cubed(smc, precision):
+    """The precision configuration (planar tanh flame, 9 species / 21
+    reactions, 3% velocity perturbations) on a 64^3 box of the 256^3 run's
+    spacing and time step: 20 SDC steps (3 Gauss-Lobatto nodes, 4 sweeps)
+    on the GPU against the FP64 oracle's 20-step state at 160 sampled cells.
+    Errors per field relative to the field's largest 20-step change and to
+    its largest value over the box.  FP64: within 1e-9 of the change (the
+    single-step bar is 1e-10; twenty steps accumulate it).  Mixed: within
+    1e-5 of the change."""
+    cells, ref, inc_max, u_max = _golden_c3()
+    wl = synth.workload("c3", seed=1, n=64)
+    U_g = conserved(wl)
+    U = synth.global_to_boxes(wl.grid, U_g)
+    with smc.Smc(wl.grid, wl.mech, {"precision": precision}) as h:
+        Ud = torch.from_numpy(U).to("cuda:0")
+        for _ in range(20):
+            h.sdc_step(Ud, wl.dt, wl.nodes, wl.sweeps, 0)
+        h.synchronize()
+        U20 = synth.boxes_to_global(wl.grid, Ud.cpu().numpy())
+    got = np.stack([U20[:, z, y, x] for z, y, x in cells], axis=1)
+    e_inc = np.abs(got - ref).max(axis=1) / inc_max
+    e_state = np.abs(got - ref).max(axis=1) / u_max
+    print(f"precision {precision}: 20-step error / change", np.array2string(e_inc, precision=2))
+    print(f"precision {precision}: 20-step error / state", np.array2string(e_state, precision=2))
+    if precision == 0:
+        assert e_inc.max() < 1e-9, e_inc
+    else:
+        assert e_inc.max() < TOL_MIXED, e_inc
+        assert e_state.max() < TOL_MIXED, e_state
+
+
+def test_mixed_rhs_of_the_bump_at_full_size_every_cell(smc):
+    """The 64^3 bump configuration (9 species), where one species' gradient
+    and pressure-gradient diffusion fluxes are each several times its net flux
+    and its face fluxes tens of times their divergence: the mixed right-hand
+    side at every cell within 1e-5 of the FP64 one (itself held to the oracle
+    at sampled cells by test_full_size_sampled_cells)."""
+    wl = synth.workload("c2", seed=1)
+    U = synth.global_to_boxes(wl.grid, conserved(wl))
+    F64 = gpu_rhs(smc, wl, U, 0)
+    Fm = gpu_rhs(smc, wl, U, 1)
+    err = relerr(Fm, F64)
+    print("c2 mixed vs FP64, every cell:", np.array2string(err, precision=2))
+    assert err.max() < TOL_MIXED, err

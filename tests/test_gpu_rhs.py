@@ -54,17 +54,20 @@ def test_rhs_c1(smc, seed):
     assert err.max() < TOL, err
 
 
-def test_rhs_c1_reference_species_mode(smc):
+@pytest.mark.parametrize("march", [0, 1])
+def test_rhs_c1_reference_species_mode(smc, march):
     wl, U, U_g = state("c1", seed=3, p_amp=0.03)
-    got = gpu_rhs(smc, wl, U, diffusion_mode=1)
+    got = gpu_rhs(smc, wl, U, diffusion_mode=1, march=march)
     err = relerr(got, oracle_rhs(wl, U_g, mode="ref"))
     assert err.max() < TOL, err
 
 
-def test_rhs_options_bulk_viscosity_and_stencil_parameters(smc):
+@pytest.mark.parametrize("march", [0, 1])
+def test_rhs_options_bulk_viscosity_and_stencil_parameters(smc, march):
     wl, U, U_g = state("c1", seed=4, p_amp=0.03)
     from oracle import stencil as ost
-    got = gpu_rhs(smc, wl, U, xi_ratio=0.6, m47=float(ost.M47_OPT), m48=float(ost.M48_OPT))
+    got = gpu_rhs(smc, wl, U, xi_ratio=0.6, m47=float(ost.M47_OPT), m48=float(ost.M48_OPT),
+                  march=march)
     err = relerr(got, oracle_rhs(wl, U_g, xi_ratio=0.6, m47=ost.M47_OPT, m48=ost.M48_OPT))
     assert err.max() < TOL, err
 
@@ -75,8 +78,8 @@ def test_rhs_no_reactions(smc):
     assert err.max() < TOL, err
 
 
-@pytest.mark.parametrize("segment", [16, 5, 64])
-def test_rhs_ragged_box_nine_species(smc, segment):
+@pytest.mark.parametrize("segment,march", [(16, 0), (5, 0), (64, 0), (5, 1), (13, 2), (64, 2)])
+def test_rhs_ragged_box_nine_species(smc, segment, march):
     """A 20 x 24 x 28 box (segments, ragged tails), 9 species / 21 reactions."""
     wl = synth.workload("c2", seed=2, n=8)
     grid = synth.single_box((20, 24, 28), (0.1 / 20, 0.1 / 24, 0.1 / 28))
@@ -84,11 +87,12 @@ def test_rhs_ragged_box_nine_species(smc, segment):
     U_g = thermo.conserved(g, wl.mech.nasa7, wl.mech.W)
     wl.grid = grid
     U = synth.global_to_boxes(grid, U_g)
-    err = relerr(gpu_rhs(smc, wl, U, segment=segment), oracle_rhs(wl, U_g))
+    err = relerr(gpu_rhs(smc, wl, U, segment=segment, march=march), oracle_rhs(wl, U_g))
     assert err.max() < TOL, err
 
 
-def test_rhs_multibox_21_species(smc):
+@pytest.mark.parametrize("march", [0, 1])
+def test_rhs_multibox_21_species(smc, march):
     """Eight uneven boxes tiling a periodic domain (ghost cells gathered from
     neighbouring boxes), 21 species / 84 reactions."""
     wl = synth.workload("c4", seed=3, n=12)
@@ -96,11 +100,12 @@ def test_rhs_multibox_21_species(smc):
     prim_g = synth.boxes_to_global(wl.grid, wl.prim)
     U_g = thermo.conserved(prim_g, wl.mech.nasa7, wl.mech.W)
     U = synth.global_to_boxes(wl.grid, U_g)
-    err = relerr(gpu_rhs(smc, wl, U), oracle_rhs(wl, U_g))
+    err = relerr(gpu_rhs(smc, wl, U, march=march), oracle_rhs(wl, U_g))
     assert err.max() < TOL, err
 
 
-def test_rhs_tiny_box_single_species(smc):
+@pytest.mark.parametrize("march", [0, 1])
+def test_rhs_tiny_box_single_species(smc, march):
     """Degenerate case: one species, no reactions, a 5 x 6 x 7 box smaller
     than two stencil widths (ghost cells wrap several times)."""
     mech = synth.make_mechanism(1, 0, 1)
@@ -113,7 +118,7 @@ def test_rhs_tiny_box_single_species(smc):
         pass
     wl = W()
     wl.grid, wl.mech = grid, mech
-    err = relerr(gpu_rhs(smc, wl, U), oracle_rhs(wl, U_g))
+    err = relerr(gpu_rhs(smc, wl, U, march=march), oracle_rhs(wl, U_g))
     assert err.max() < TOL, err
 
 
@@ -149,8 +154,8 @@ def conditioning_floor(U_g, cells, mech, dx, scale):
     return ref.astype(np.float64), np.abs((pert - ref).astype(np.float64)).max(axis=1) / scale
 
 
-@pytest.mark.parametrize("name", ["c2", "c4"])
-def test_rhs_full_size_sampled_cells(smc, name):
+@pytest.mark.parametrize("name,march", [("c2", 0), ("c4", 0), ("c2", 1), ("c4", 2)])
+def test_rhs_full_size_sampled_cells(smc, name, march):
     """Full-size configurations, in the launch configuration the benchmark
     uses, checked at sampled cells that the oracle evaluates one by one, in
     extended precision (np.longdouble).
@@ -166,7 +171,7 @@ def test_rhs_full_size_sampled_cells(smc, name):
     prim_g = synth.boxes_to_global(g, wl.prim)
     U_g = thermo.conserved(prim_g, wl.mech.nasa7, wl.mech.W)
     U = synth.global_to_boxes(g, U_g)
-    F = synth.boxes_to_global(g, gpu_rhs(smc, wl, U))
+    F = synth.boxes_to_global(g, gpu_rhs(smc, wl, U, march=march))
     cells = _sample_cells(np.random.default_rng(0), g, 10)
     full_scale = np.abs(F).reshape(F.shape[0], -1).max(axis=1)
     ref, floor = conditioning_floor(U_g, cells, wl.mech, g.dx, full_scale)
@@ -204,12 +209,12 @@ def test_bad_arguments(smc):
 @pytest.mark.parametrize("precision", [0, 1])
 def test_tile_choices_give_identical_results_and_autotune(smc, precision):
     """Segment length and x-line layout change only the schedule: every
-    choice gives the same bits for a given line kernel (and the three
-    sliding-window variants the same bits as each other); the per-face and
-    sliding-window kernels agree to the mixed tolerance; the autotuner picks
-    one of the choices."""
+    choice gives the same bits for a given line kernel, and the
+    sliding-window variants (chunk length, occupancy) the same bits as each
+    other; the FP64 per-face and sliding-window kernels agree to the FP64
+    tolerance; the autotuner picks one of the choices."""
     wl, U, U_g = state("c1", seed=7, p_amp=0.03)
-    marches = (0, 1, 2, 3) if precision else (0,)
+    marches = (0, 1, 2, 3) if precision else (0, 1, 2)
     ref = {}
     for mv in marches:
         outs = []
@@ -222,9 +227,14 @@ def test_tile_choices_give_identical_results_and_autotune(smc, precision):
         ref[mv] = outs[0]
     if precision:
         assert relerr(ref[1], oracle_rhs(wl, U_g)).max() < TOL_MIXED
-        assert relerr(ref[1], ref[0]).max() < TOL_MIXED
-        # the sliding-window variants differ only in chunking and occupancy
+        # 0 is taken as 1; the variants differ only in chunking and occupancy
+        assert np.array_equal(ref[1], ref[0])
         assert np.array_equal(ref[1], ref[2]) and np.array_equal(ref[1], ref[3])
+    else:
+        ora = oracle_rhs(wl, U_g)
+        for mv in marches:
+            assert relerr(ref[mv], ora).max() < TOL, mv
+        assert np.array_equal(ref[1], ref[2])
     with smc.Smc(wl.grid, wl.mech, {"precision": precision}) as h:
         choice = h.autotune(dev(U))
         assert choice["segment"] in (8, 16, 32, 64) and choice["x_layout"] in (0, 1)

@@ -207,8 +207,11 @@ def test_eval_counts_reproduce_table_mrsdc_runtime(smc):
 def test_sdc_residual_early_exit_matches_oracle(smc):
     """eq. residual with the early exit (eps = 0.5, up to 14 sweeps): the
     library's residual after every sweep equals the oracle's while it is far
-    above rounding, both stop within one sweep of each other once it
-    stagnates, and the state agrees."""
+    above rounding, and the state agrees.  The exit compares two successive
+    residuals (stop once |R^(k-1)| / |R^k| < 1 + eps); once both are at the
+    rounding floor their ratio is rounding noise on either side, so the two
+    implementations may stop one sweep apart -- but only there: every sweep
+    before the stop matches, and the residual at the stop is at the floor."""
     wl, U, U_g = state("c1", seed=2, p_amp=0.03)
     with smc.Smc(wl.grid, wl.mech, {"sdc_exit": 0.5}) as h:
         Ud = dev(U)
@@ -221,6 +224,8 @@ def test_sdc_residual_early_exit_matches_oracle(smc):
     got = st["residual"]
     assert len(got) == st["sweeps_done"] < 14
     assert abs(st["sweeps_done"] - len(hist)) <= 1
+    if st["sweeps_done"] != len(hist):
+        assert max(got[-1], hist[-1]) < 1e-11, (got, hist)
     assert st["n_rhs"] == 1 + 2 * st["sweeps_done"]
     for g, o in zip(got, hist):
         if o > 1e-11:
