@@ -557,8 +557,6 @@ def main():
         if args.tiles:                        # a fixed schedule (profiling runs)
             seg, xl, mv, *pers = (int(v) for v in args.tiles.split(","))
             pers = pers[0] if pers else 0
-            if precision == 0 and mv == 3:
-                mv = 1
             h.set_option("segment", seg)
             h.set_option("x_layout", xl)
             h.set_option("march", mv)

@@ -135,11 +135,13 @@ enum {
                                   the box layout, 1 read an x-slowest copy made once per
                                   evaluation (nQ + 9 more ghosted planes of device memory) */
   SMC_OPT_MARCH = 14,          /* stencil-line kernel of the current precision.  FP64: 0 (default)
-                                  evaluates every face from its 8-point window; 1, 2 slide
+                                  evaluates every face from its 8-point window; 1, 2, 3 slide
                                   9-cell register windows along the line, one load per field
-                                  and cell, in chunks of 16 / 32 cells.  Mixed: 1, 2, 3 slide
-                                  windows in chunks of 16 / 32 / 16 cells sized for 3 / 3 / 4
-                                  resident blocks per SM (0 is taken as 1; default 1) */
+                                  and cell, in chunks of 16 / 32 / 8 cells (3 also keeps the
+                                  pressure products of every face in shared memory for the
+                                  species terms, at 2 resident blocks per SM).  Mixed: 1, 2, 3
+                                  slide windows in chunks of 16 / 32 / 16 cells sized for
+                                  3 / 3 / 4 resident blocks per SM (0 is taken as 1; default 1) */
   SMC_OPT_RATES = 15,          /* production rates under SMC_OPT_PRECISION = 1: 0 (default)
                                   FP64 like the FP64 path; 1 FP32 mantissas after FP64 Gibbs
                                   energies, reaction exponents and exponent reductions

@@ -225,11 +225,22 @@ smc_status build_lines(smc_handle *h) {
       const int nd = n[d];
       int nseg = (nd + h->segment - 1) / h->segment;
       if (nseg < 1) nseg = 1;
-      for (int sgi = 0; sgi < nseg; ++sgi) {
-        const int s0 = (int)((long long)nd * sgi / nseg);
-        const int s1 = (int)((long long)nd * (sgi + 1) / nseg);
-        for (int t1 = 0; t1 < n[e1]; ++t1)
-          for (int t0 = 0; t0 < n[e0]; ++t0) {
+      // Item order = thread order.  y and z lines: consecutive threads take
+      // neighbouring x lines (their loads are consecutive addresses).  x
+      // lines in the box layout: consecutive threads take consecutive
+      // segments of one row, so a warp's loads fall in a few cache lines
+      // instead of one line per thread.
+      const bool row_major = d == 0;
+      const int n_outer = row_major ? n[e1] * n[e0] : nseg;
+      const int n_inner = row_major ? nseg : n[e1] * n[e0];
+      for (int o = 0; o < n_outer; ++o)
+        for (int q = 0; q < n_inner; ++q) {
+          const int sgi = row_major ? q : o;
+          const int row = row_major ? o : q;
+          const int t1 = row / n[e0], t0 = row % n[e0];
+          const int s0 = (int)((long long)nd * sgi / nseg);
+          const int s1 = (int)((long long)nd * (sgi + 1) / nseg);
+          {
             LineItem L;
             long long go = B.off_g, io = B.off_i;
             int crd[3];
@@ -255,21 +266,29 @@ smc_status build_lines(smc_handle *h) {
     CUDA_TRY(h, cudaMemcpy(h->d_lines[d], items.data(), items.size() * sizeof(LineItem),
                            cudaMemcpyHostToDevice));
     if (d == 0) {
-      // the same x segments addressed in the [x][z][y] copy of each box
-      std::vector<LineItem> xt = items;
-      size_t t = 0;
+      // the same x segments addressed in the [x][z][y] copy of each box, in
+      // their own order: segments outer, y inner (consecutive threads read
+      // consecutive addresses of that copy)
+      std::vector<LineItem> xt;
+      xt.reserve(items.size());
       for (int b = 0; b < h->nboxes; ++b) {
         const Box &B = h->boxes[b];
         int nseg = (B.nx + h->segment - 1) / h->segment;
         if (nseg < 1) nseg = 1;
         for (int sgi = 0; sgi < nseg; ++sgi) {
           const int s0 = (int)((long long)B.nx * sgi / nseg);
+          const int s1 = (int)((long long)B.nx * (sgi + 1) / nseg);
           for (int z = 0; z < B.nz; ++z)
             for (int y = 0; y < B.ny; ++y) {
-              xt[t].g0 = B.off_g + ((long long)(s0 + SMC_GHOST) * B.gz + (z + SMC_GHOST)) * B.gy +
-                         (y + SMC_GHOST);
-              xt[t].sg = B.gy * B.gz;
-              ++t;
+              LineItem L;
+              L.g0 = B.off_g + ((long long)(s0 + SMC_GHOST) * B.gz + (z + SMC_GHOST)) * B.gy +
+                     (y + SMC_GHOST);
+              L.i0 = B.off_i + ((long long)z * B.ny + y) * B.nx + s0;
+              L.sg = B.gy * B.gz;
+              L.si = 1;
+              L.len = s1 - s0;
+              L.pad = 0;
+              xt.push_back(L);
             }
         }
       }
@@ -1293,8 +1312,6 @@ smc_status smc_set_option(smc_handle *h, int key, double v) {
       return SMC_OK;
     case SMC_OPT_MARCH:
       if (v < 0 || v > 3 || v != floor(v)) return fail(h, SMC_ERR_ARG, "march kernel must be 0..3");
-      if (v == 3.0 && h->precision != 1)
-        return fail(h, SMC_ERR_ARG, "FP64 line kernels are 0..2");
       h->march[h->precision == 1] = (int)v;
       return SMC_OK;
     case SMC_OPT_FINE_REPEAT:
@@ -1403,7 +1420,7 @@ smc_status smc_autotune(smc_handle *h, const double *U, int *segment, int *x_lay
   h->cache_kind = 0;   // slot 0 is overwritten
   const int mixed = h->precision == 1;
   const int segs[4] = {8, 16, 32, 64};
-  const int mv0 = mixed ? 1 : 0, nvar = mixed ? 4 : 3;   // mixed: the sliding-window kernels
+  const int mv0 = mixed ? 1 : 0, nvar = 4;   // mixed: the sliding-window kernels
   float best = 1e30f;
   int best_seg = h->segment, best_xt = h->xt[mixed], best_mv = h->march[mixed];
   cudaEvent_t a, b;

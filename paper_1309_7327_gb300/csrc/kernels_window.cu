@@ -133,14 +133,19 @@ __device__ __forceinline__ double flux_d(const Win &x, int r) {
 }
 
 // CH: cells per chunk.  The three per-cell arrays live in dynamic shared
-// memory, 3 CH NT doubles.
-template <int DIR, int CH>
-__global__ void __launch_bounds__(NT, 3) k_march_w(const DevState s, const ParamsW P,
-                                                   double *__restrict__ dU, int first) {
+// memory, 3 CH NT doubles.  WP: the pressure products w = M (p - p_3) of
+// the chunk's CH + 1 faces are also kept in shared memory (8 (CH + 1) NT
+// more doubles), formed once in the heat pass and read by every species'
+// pressure term, instead of formed again for every species; MINB is the
+// resident blocks per SM the registers are sized for.
+template <int DIR, int CH, bool WP, int MINB>
+__global__ void __launch_bounds__(NT, MINB) k_march_w(const DevState s, const ParamsW P,
+                                                      double *__restrict__ dU, int first) {
   extern __shared__ double w_smem[];
   double(*sE)[NT] = reinterpret_cast<double(*)[NT]>(w_smem);
   double(*sV)[NT] = sE + CH;
   double(*sN)[NT] = sV + CH;
+  double(*sW)[NT] = sN + CH;       // [(face * 8 + m)][thread], WP only
   const int tid = threadIdx.x;
   constexpr int E_ = (DIR + 1) % 3, F_ = (DIR + 2) % 3;
   const int ns = s.ns, mode = s.opt.mode, ref = s.opt.ref;
@@ -238,11 +243,15 @@ __global__ void __launch_bounds__(NT, 3) k_march_w(const DevState s, const Param
       }
       double w[8];
       mv(P, f, 0, w);
+      if (WP && pass == 1)
+        for (int m = 0; m < 8; ++m) sW[m][tid] = w[m];
       double H = ds(a, 0, w);
 #pragma unroll 1
       for (int c = 0; c < n; ++c) {
         if (pass == 1 && mode == 0) sV[c][tid] = -x.q(Q_SB, c) * Dc(P, f);
         mv(P, f, 1, w);
+        if (WP && pass == 1)
+          for (int m = 0; m < 8; ++m) sW[(c + 1) * 8 + m][tid] = w[m];
         const double H2 = ds(a, 1, w);
         sE[c][tid] += H2 - H;
         H = H2;
@@ -354,14 +363,22 @@ __global__ void __launch_bounds__(NT, 3) k_march_w(const DevState s, const Param
         Yk[i] = mode == 0 ? x.q(qY(ns) + k, i - 4) : 0.0;
       }
       double w[8];
-      mv(P, p, 0, w);
+      if (WP) {
+        for (int m = 0; m < 8; ++m) w[m] = sW[m][tid];
+      } else {
+        mv(P, p, 0, w);
+      }
       double H = ds(B, 0, w);
 #pragma unroll 1
       for (int c = 0; c < n; ++c) {
         double o = -Dc(P, Fk);
         if (mode == 0) o = fma(Dc(P, Yk), sV[c][tid], o);
         if (narrow) {
-          mv(P, p, 1, w);
+          if (WP) {
+            for (int m = 0; m < 8; ++m) w[m] = sW[(c + 1) * 8 + m][tid];
+          } else {
+            mv(P, p, 1, w);
+          }
           const double H2 = ds(B, 1, w);
           o += H2 - H;
           sN[c][tid] += H2 - H;
@@ -406,29 +423,32 @@ __global__ void __launch_bounds__(NT, 3) k_march_w(const DevState s, const Param
   }
 }
 
-template <int CH>
+template <int CH, bool WP, int MINB>
 void launch_variant(const DevState &s, int dir, const ParamsW &P, double *dU, int first,
                     int blocks, cudaStream_t st) {
-  const size_t smem = 3 * CH * NT * sizeof(double);
+  const size_t smem = (3 * CH + (WP ? 8 * (CH + 1) : 0)) * NT * sizeof(double);
   // the attribute is per device: set it once per device, on the first
   // (eager) launch, before any stream capture
   static bool attr_set[64] = {};
   int dev = 0;
   cudaGetDevice(&dev);
   if (dev >= 0 && dev < 64 && !attr_set[dev]) {
-    cudaFuncSetAttribute(k_march_w<0, CH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaFuncSetAttribute(k_march_w<1, CH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaFuncSetAttribute(k_march_w<2, CH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(k_march_w<0, CH, WP, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem);
+    cudaFuncSetAttribute(k_march_w<1, CH, WP, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem);
+    cudaFuncSetAttribute(k_march_w<2, CH, WP, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem);
     attr_set[dev] = true;
   }
   if (s.opt.persistent) {
     static int cache[64] = {};
-    const int r = resident_blocks(k_march_w<1, CH>, NT, smem, cache);
+    const int r = resident_blocks(k_march_w<1, CH, WP, MINB>, NT, smem, cache);
     if (blocks > r) blocks = r;
   }
-  if (dir == 0) k_march_w<0, CH><<<blocks, NT, smem, st>>>(s, P, dU, first);
-  else if (dir == 1) k_march_w<1, CH><<<blocks, NT, smem, st>>>(s, P, dU, first);
-  else k_march_w<2, CH><<<blocks, NT, smem, st>>>(s, P, dU, first);
+  if (dir == 0) k_march_w<0, CH, WP, MINB><<<blocks, NT, smem, st>>>(s, P, dU, first);
+  else if (dir == 1) k_march_w<1, CH, WP, MINB><<<blocks, NT, smem, st>>>(s, P, dU, first);
+  else k_march_w<2, CH, WP, MINB><<<blocks, NT, smem, st>>>(s, P, dU, first);
 }
 
 }  // namespace
@@ -443,8 +463,9 @@ void launch_march_w(const DevState &s, int dir, double *dUdt, int first, int var
   const long long n = s.nlines[dir];
   if (n == 0) return;
   const int blocks = (int)((n + NT - 1) / NT);
-  if (variant == 2) launch_variant<32>(s, dir, P, dUdt, first, blocks, st);
-  else launch_variant<16>(s, dir, P, dUdt, first, blocks, st);
+  if (variant == 3) launch_variant<8, true, 2>(s, dir, P, dUdt, first, blocks, st);
+  else if (variant == 2) launch_variant<32, false, 3>(s, dir, P, dUdt, first, blocks, st);
+  else launch_variant<16, false, 3>(s, dir, P, dUdt, first, blocks, st);
 }
 
 }  // namespace smc

@@ -201,7 +201,8 @@ int resident_blocks(K f, int threads, size_t smem, int *cache) {
 void launch_prim(const DevState &s, const double *U, cudaStream_t st);
 void launch_grad(const DevState &s, cudaStream_t st);
 void launch_march(const DevState &s, int dir, double *dUdt, int first, cudaStream_t st);
-// FP64 sliding-window line kernel (variant 1: 16-cell chunks, 2: 32-cell chunks)
+// FP64 sliding-window line kernel (variant 1: 16-cell chunks, 2: 32-cell chunks,
+// 3: 8-cell chunks with the pressure products of every face kept in shared memory)
 void launch_march_w(const DevState &s, int dir, double *dUdt, int first, int variant,
                     cudaStream_t st);
 void launch_final(const DevState &s, double *dUdt, int transport, int chemistry, cudaStream_t st);
