@@ -49,6 +49,8 @@ struct smc_handle {
   Box *d_boxes = nullptr;
   int *d_gmap = nullptr;
   long long *d_imap = nullptr;
+  long long *d_halo_dst = nullptr, *d_halo_src = nullptr;   // ghost cell -> its periodic image
+  long long nhalo = 0;
   LineItem *d_lines[3] = {nullptr, nullptr, nullptr};
   long long nlines[3] = {0, 0, 0};
   LineItem *d_lines_xt = nullptr;       // x lines in the x-slowest (transposed) layout
@@ -194,6 +196,9 @@ DevState state(smc_handle *h) {
   s.nx_domain = h->nx_domain;
   s.bc_cells = h->d_bc;
   s.n_bc = (long long)h->hbc.size();
+  s.halo_dst = h->d_halo_dst;
+  s.halo_src = h->d_halo_src;
+  s.nhalo = h->nhalo;
   return s;
 }
 
@@ -358,7 +363,12 @@ smc_status eval_rhs(smc_handle *h, const double *U, double *F, int transport, in
   if (mixed && !h->d_dUf) CUDA_TRY(h, dalloc(h, &h->d_dUf, (size_t)h->nv * h->ncells));
   {
     Timed t(h, SMC_K_PRIM);
-    if (mixed) launch_prim_m(s, U, h->stream); else launch_prim(s, U, h->stream);
+    if (mixed) {
+      launch_prim_m(s, U, h->stream);
+    } else {
+      launch_prim_interior(s, U, h->stream);
+      launch_halo(s, nQ(h->ns), 8, h->stream);
+    }
   }
   if (transport) {
     {
@@ -1042,6 +1052,28 @@ smc_status smc_create(const smc_grid *grid, const smc_mechanism *mech, const smc
   TRY_ALLOC(cudaMemcpy(h->d_gmap, gmap.data(), gmap.size() * sizeof(int), cudaMemcpyHostToDevice));
   TRY_ALLOC(dalloc(h, &h->d_imap, (size_t)h->ncells));
   TRY_ALLOC(cudaMemcpy(h->d_imap, imap.data(), imap.size() * sizeof(long long), cudaMemcpyHostToDevice));
+  {
+    // the halo list: every ghost cell with the ghosted index of its image
+    std::vector<char> inner((size_t)h->nghost, 0);
+    for (long long i = 0; i < h->ncells; ++i) inner[(size_t)imap[(size_t)i]] = 1;
+    std::vector<long long> hd, hs;
+    hd.reserve((size_t)(h->nghost - h->ncells));
+    hs.reserve((size_t)(h->nghost - h->ncells));
+    for (long long g = 0; g < h->nghost; ++g)
+      if (!inner[(size_t)g]) {
+        hd.push_back(g);
+        hs.push_back(imap[(size_t)gmap[(size_t)g]]);
+      }
+    h->nhalo = (long long)hd.size();
+    if (h->nhalo > 0) {
+      TRY_ALLOC(dalloc(h, &h->d_halo_dst, hd.size()));
+      TRY_ALLOC(dalloc(h, &h->d_halo_src, hs.size()));
+      TRY_ALLOC(cudaMemcpy(h->d_halo_dst, hd.data(), hd.size() * sizeof(long long),
+                           cudaMemcpyHostToDevice));
+      TRY_ALLOC(cudaMemcpy(h->d_halo_src, hs.data(), hs.size() * sizeof(long long),
+                           cudaMemcpyHostToDevice));
+    }
+  }
   if (!h->hbc.empty()) {
     TRY_ALLOC(dalloc(h, &h->d_bc, h->hbc.size()));
     TRY_ALLOC(cudaMemcpy(h->d_bc, h->hbc.data(), h->hbc.size() * sizeof(BcCell), cudaMemcpyHostToDevice));
@@ -1076,6 +1108,8 @@ smc_status smc_destroy(smc_handle *h) {
   cudaFree(h->d_boxes);
   cudaFree(h->d_gmap);
   cudaFree(h->d_imap);
+  cudaFree(h->d_halo_dst);
+  cudaFree(h->d_halo_src);
   for (int d = 0; d < 3; ++d) cudaFree(h->d_lines[d]);
   cudaFree(h->d_lines_xt);
   cudaFree(h->d_xt_tiles);

@@ -78,15 +78,19 @@ __device__ __forceinline__ f2 mulf(f2 a, float b) {
 }
 
 // ------------------------------------------------------------ k_prim_m
+// INTERIOR: one thread per interior cell (ghost cells filled by k_halo);
+// otherwise one per ghosted cell through the gather map.
+template <bool INTERIOR>
 __global__ void __launch_bounds__(128) k_prim_m(const DevState s, const double *__restrict__ U) {
   const Mech &m = *s.mech;
   const int ns = s.ns;
   const long long NG = s.nghost, NI = s.ncells;
   float *__restrict__ Qf = reinterpret_cast<float *>(s.Q);
   const int mode = s.opt.mode, ref = s.opt.ref;
-  for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < NG;
-       g += (long long)gridDim.x * blockDim.x) {
-    const long long src = s.gmap[g];
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < (INTERIOR ? NI : NG);
+       t += (long long)gridDim.x * blockDim.x) {
+    const long long g = INTERIOR ? s.imap[t] : t;
+    const long long src = INTERIOR ? t : (long long)s.gmap[t];
     const double rho = U[src];
     const double invrho = 1.0 / rho;
     const double u = U[NI + src] * invrho;
@@ -295,7 +299,12 @@ static int grid_for(long long n, int block) {
 }
 
 void launch_prim_m(const DevState &s, const double *U, cudaStream_t st) {
-  k_prim_m<<<grid_for(s.nghost, 128), 128, 0, st>>>(s, U);
+  if (s.nhalo > 0) {
+    k_prim_m<true><<<grid_for(s.ncells, 128), 128, 0, st>>>(s, U);
+    launch_halo(s, nQm(s.ns), 4, st);
+  } else {
+    k_prim_m<false><<<grid_for(s.nghost, 128), 128, 0, st>>>(s, U);
+  }
 }
 
 void launch_grad_m(const DevState &s, cudaStream_t st) {

@@ -19,15 +19,20 @@ namespace smc {
 #define QF(f, g) __ldg(Q + (size_t)(f) * NG + (g))
 
 // ---------------------------------------------------------------- k_prim
+// INTERIOR: one thread per interior cell (the ghost cells are then filled by
+// k_halo from their periodic images); otherwise one per ghosted cell, each
+// reading U through the ghost-cell gather map.
+template <bool INTERIOR>
 __global__ void __launch_bounds__(128) k_prim(const DevState s, const double *__restrict__ U) {
   const Mech &m = *s.mech;
   const int ns = s.ns;
   const long long NG = s.nghost, NI = s.ncells;
   double *__restrict__ Q = s.Q;
   const int mode = s.opt.mode, ref = s.opt.ref;
-  for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < NG;
-       g += (long long)gridDim.x * blockDim.x) {
-    const long long src = s.gmap[g];
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < (INTERIOR ? NI : NG);
+       t += (long long)gridDim.x * blockDim.x) {
+    const long long g = INTERIOR ? s.imap[t] : t;
+    const long long src = INTERIOR ? t : (long long)s.gmap[t];
     const double rho = U[src];
     const double invrho = 1.0 / rho;
     const double u = U[NI + src] * invrho;
@@ -53,7 +58,10 @@ __global__ void __launch_bounds__(128) k_prim(const DevState s, const double *__
     const double p = rho * kRu * T * wmix;
     const double invp = 1.0 / p;
     const double inv_wmix = 1.0 / wmix;
-    const double eta = m.eta_ref * pow(T * m.inv_T_ref, m.eta_exp);
+    // eta_ref (T / T_ref)^eta_exp as exp(eta_exp ln(T / T_ref)) with the
+    // library's exponential (one log and one table exponential instead of a
+    // general power)
+    const double eta = m.eta_ref * fast_exp(m, m.eta_exp * log(T * m.inv_T_ref));
     const double xi = s.opt.xi_ratio * eta;
     const double lam = cpm * eta * m.inv_Pr;
     const double rd0 = lam / cpm;
@@ -469,7 +477,47 @@ static int grid_for(long long n, int block) {
 }
 
 void launch_prim(const DevState &s, const double *U, cudaStream_t st) {
-  k_prim<<<grid_for(s.nghost, 128), 128, 0, st>>>(s, U);
+  k_prim<false><<<grid_for(s.nghost, 128), 128, 0, st>>>(s, U);
+}
+
+// Copy every plane of the primitive scratch from each ghost cell's periodic
+// image (an interior cell of some box) to the ghost cell: the halo fill of
+// the box array (Sec. 4), done once on the primitives instead of repeating
+// the temperature solve and transport evaluation at every ghost cell.
+template <typename T>
+__global__ void __launch_bounds__(256) k_halo(const long long *__restrict__ dst,
+                                              const long long *__restrict__ src, long long nh,
+                                              T *__restrict__ Q, long long NG, int planes) {
+  // blockIdx.y picks a group of 8 planes: eight independent loads in flight
+  // per thread before the stores
+  const int p0 = blockIdx.y * 8;
+  for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < nh;
+       j += (long long)gridDim.x * blockDim.x) {
+    const long long gd = dst[j], gs = src[j];
+    T v[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q)
+      if (p0 + q < planes) v[q] = Q[(size_t)(p0 + q) * NG + gs];
+#pragma unroll
+    for (int q = 0; q < 8; ++q)
+      if (p0 + q < planes) Q[(size_t)(p0 + q) * NG + gd] = v[q];
+  }
+}
+
+void launch_prim_interior(const DevState &s, const double *U, cudaStream_t st) {
+  k_prim<true><<<grid_for(s.ncells, 128), 128, 0, st>>>(s, U);
+}
+
+void launch_halo(const DevState &s, int planes, int esize, cudaStream_t st) {
+  if (s.nhalo == 0) return;
+  long long bx = (s.nhalo + 255) / 256;
+  if (bx > 152LL * 16) bx = 152LL * 16;
+  const dim3 grid((unsigned)bx, (unsigned)((planes + 7) / 8));
+  if (esize == 8)
+    k_halo<double><<<grid, 256, 0, st>>>(s.halo_dst, s.halo_src, s.nhalo, s.Q, s.nghost, planes);
+  else
+    k_halo<float><<<grid, 256, 0, st>>>(s.halo_dst, s.halo_src, s.nhalo,
+                                        reinterpret_cast<float *>(s.Q), s.nghost, planes);
 }
 
 void launch_grad(const DevState &s, cudaStream_t st) {

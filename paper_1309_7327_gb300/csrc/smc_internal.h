@@ -171,6 +171,9 @@ struct DevState {
   int nx_domain;                  // cells of the domain along x
   const BcCell *bc_cells;         // the cells next to the x ends (x_outflow only)
   long long n_bc;
+  const long long *halo_dst;      // ghost cells (ghosted index) ...
+  const long long *halo_src;      // ... and the ghosted index of their periodic image
+  long long nhalo;                // 0: primitives are evaluated at every ghosted cell
 };
 
 // Boundary-lowered x-direction terms at the cells next to the x ends; they
@@ -198,7 +201,13 @@ int resident_blocks(K f, int threads, size_t smem, int *cache) {
   return cache[dev];
 }
 
+// Primitives at every ghosted cell, each through the gather map (no halo list needed).
 void launch_prim(const DevState &s, const double *U, cudaStream_t st);
+// Primitives at the interior cells only, then launch_halo.
+void launch_prim_interior(const DevState &s, const double *U, cudaStream_t st);
+// Fill the ghost cells of `planes` primitive planes (element size 8 or 4)
+// from their periodic images through the halo list (s.nhalo entries).
+void launch_halo(const DevState &s, int planes, int esize, cudaStream_t st);
 void launch_grad(const DevState &s, cudaStream_t st);
 void launch_march(const DevState &s, int dir, double *dUdt, int first, cudaStream_t st);
 // FP64 sliding-window line kernel (variant 1: 16-cell chunks, 2: 32-cell chunks,

@@ -90,7 +90,7 @@ def _compositions(ns: int, rng) -> tuple[np.ndarray, np.ndarray]:
         ne, span = 2, 4
     else:
         weights = np.array([1.008, 12.011, 15.999])
-        ne, span = 3, (3 if ns <= 26 else 4)
+        ne, span = 3, (3 if ns <= 26 else 4 if ns <= 63 else 5)
     atoms = [tuple(1 if i == j else 0 for i in range(ne)) for j in range(ne)]
     lattice = [v for v in itertools.product(range(span), repeat=ne)
                if sum(v) > 0 and v not in atoms]

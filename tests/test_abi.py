@@ -144,3 +144,13 @@ def test_create_rejects_bad_box_arrays_without_touching_the_gpu(lib):
         assert e.value.status == smc.SMC_ERR_ARG, what
         assert what in str(e.value) or what == "outside" and "outside" in str(e.value), \
             (what, str(e.value))
+
+
+def test_create_rejects_more_species_than_the_limit_without_touching_the_gpu(lib):
+    """64 species is the largest mechanism the kernels are built for; 65 is
+    refused during host validation."""
+    from paper_1309_7327_gb300 import synth
+    m = synth.make_mechanism(65, 10, 3)
+    with pytest.raises(smc.SmcError) as e:
+        smc.Smc(synth.single_box(8, 0.1), m)
+    assert e.value.status == smc.SMC_ERR_ARG
