@@ -231,7 +231,7 @@ def pipe_peaks(local: int) -> dict:
     sampler.start()
     out = {}
     for name, kind, iters in (("fp64", 0, 150_000), ("fp32", 1, 8_000_000),
-                              ("fp32x2", 2, 4_000_000)):
+                              ("fp32x2", 2, 4_000_000), ("fp64_one_lane", 3, 150_000)):
         smc.smc_fma_throughput(kind, max(1, iters // 10))
         fl, ms, sms = smc.smc_fma_throughput(kind, iters)
         out[name + "_tflops"] = fl / 1e12

@@ -373,14 +373,15 @@ smc_status smc_react_integrate(smc_handle *h, const double *U, const double *G, 
  * the denominator of the arithmetic rooflines (Sec. 2.3 counts the flops of
  * the stencils; this measures the rate they can run at on this GPU).
  *   kind 0: FP64 FMA (DFMA); 1: FP32 FMA; 2: paired FP32 FMA (two per lane
- *   and instruction).
+ *   and instruction); 3: FP64 FMA on one active lane per warp (flops of the
+ *   active lanes: what scalar FP64 work costs in warp-cooperative code).
  * One untimed launch, then one launch of multiProcessorCount x 4 blocks of
  * 256 threads, each thread running 8 independent FMA chains for `iters`
  * iterations, timed with CUDA events on a private stream.  *flops_per_s
  * receives 2 x FMAs / s (required), *ms the timed launch's duration and
  * *sm_count the device's SM count (both may be NULL).  Allocates and frees
  * one small device buffer and synchronises.  SMC_ERR_ARG for kind outside
- * 0..2 or iters outside 1..2^40, SMC_ERR_OOM, SMC_ERR_CUDA. */
+ * 0..3 or iters outside 1..2^40, SMC_ERR_OOM, SMC_ERR_CUDA. */
 smc_status smc_fma_throughput(int kind, long long iters, double *flops_per_s, double *ms,
                               int *sm_count);
 

@@ -50,6 +50,25 @@ __global__ void __launch_bounds__(kThreads) k_ffma(float *out, long long iters, 
   out[blockIdx.x * (long long)blockDim.x + threadIdx.x] = s;
 }
 
+// FP64 FMAs with one active lane per warp (the other lanes skip the loop):
+// what scalar FP64 work costs inside warp-cooperative code
+__global__ void __launch_bounds__(kThreads) k_dfma_lane0(double *out, long long iters, double a,
+                                                         double b) {
+  double s = 0.0;
+  if ((threadIdx.x & 31) == 0) {
+    double x[kChains];
+#pragma unroll
+    for (int j = 0; j < kChains; ++j) x[j] = (threadIdx.x + j) * 1e-3;
+    for (long long i = 0; i < iters; ++i) {
+#pragma unroll
+      for (int j = 0; j < kChains; ++j) x[j] = fma(x[j], a, b);
+    }
+#pragma unroll
+    for (int j = 0; j < kChains; ++j) s += x[j];
+  }
+  out[blockIdx.x * (long long)blockDim.x + threadIdx.x] = s;
+}
+
 // two FP32 FMAs per lane and instruction (the paired form the mixed line
 // kernels use for their stencil products)
 __global__ void __launch_bounds__(kThreads) k_ffma2(float *out, long long iters, float a, float b) {
@@ -73,7 +92,7 @@ __global__ void __launch_bounds__(kThreads) k_ffma2(float *out, long long iters,
 extern "C" smc_status smc_fma_throughput(int kind, long long iters, double *flops_per_s,
                                          double *ms, int *sm_count) {
   using namespace smc;
-  if (kind < 0 || kind > 2 || iters < 1 || iters > (1LL << 40) || !flops_per_s) return SMC_ERR_ARG;
+  if (kind < 0 || kind > 3 || iters < 1 || iters > (1LL << 40) || !flops_per_s) return SMC_ERR_ARG;
   int dev = 0;
   cudaDeviceProp prop;
   if (cudaGetDevice(&dev) != cudaSuccess || cudaGetDeviceProperties(&prop, dev) != cudaSuccess)
@@ -97,7 +116,8 @@ extern "C" smc_status smc_fma_throughput(int kind, long long iters, double *flop
       if (rep == 1) cudaEventRecord(e0, st);
       if (kind == 0) k_dfma<<<blocks, kThreads, 0, st>>>((double *)out, it, 0.999999, 1e-7);
       else if (kind == 1) k_ffma<<<blocks, kThreads, 0, st>>>((float *)out, it, 0.999999f, 1e-7f);
-      else k_ffma2<<<blocks, kThreads, 0, st>>>((float *)out, it, 0.999999f, 1e-7f);
+      else if (kind == 2) k_ffma2<<<blocks, kThreads, 0, st>>>((float *)out, it, 0.999999f, 1e-7f);
+      else k_dfma_lane0<<<blocks, kThreads, 0, st>>>((double *)out, it, 0.999999, 1e-7);
       if (rep == 1) cudaEventRecord(e1, st);
       if (cudaGetLastError() != cudaSuccess) rc = SMC_ERR_CUDA;
     }
@@ -111,7 +131,8 @@ extern "C" smc_status smc_fma_throughput(int kind, long long iters, double *flop
   cudaFree(out);
   if (rc != SMC_OK) return rc;
   const double fma_per_thread = (double)iters * kChains * (kind == 2 ? 2.0 : 1.0);
-  *flops_per_s = 2.0 * fma_per_thread * (double)threads / (t * 1e-3);
+  const double active = kind == 3 ? (double)threads / 32.0 : (double)threads;
+  *flops_per_s = 2.0 * fma_per_thread * active / (t * 1e-3);
   if (ms) *ms = t;
   if (sm_count) *sm_count = sms;
   return SMC_OK;

@@ -25,7 +25,9 @@ def test_fma_throughput_is_measured_for_each_pipe(smc):
     clk = 2.5e9
     for fl in res.values():
         assert fl < props.multi_processor_count * 1024 * 2 * clk
+    fl1, _, _ = smc.smc_fma_throughput(3, 20_000)
+    assert 0 < fl1 <= res[0] * 1.05
     with pytest.raises(smc.SmcError):
-        smc.smc_fma_throughput(3, 10)
+        smc.smc_fma_throughput(4, 10)
     with pytest.raises(smc.SmcError):
         smc.smc_fma_throughput(0, 0)
