@@ -140,8 +140,10 @@ enum {
                                   and cell, in chunks of 16 / 32 / 8 cells (3 also keeps the
                                   pressure products of every face in shared memory for the
                                   species terms, at 2 resident blocks per SM).  Mixed: 1, 2, 3
-                                  slide windows in chunks of 16 / 32 / 16 cells sized for
-                                  3 / 3 / 4 resident blocks per SM (0 is taken as 1; default 1) */
+                                  slide windows in chunks of 16 / 32 / 8 cells (3 keeps the
+                                  pressure products of both faces of every cell in shared
+                                  memory, at 2 resident blocks per SM; 0 is taken as 1;
+                                  default 1) */
   SMC_OPT_RATES = 15,          /* production rates under SMC_OPT_PRECISION = 1: 0 (default)
                                   FP64 like the FP64 path; 1 FP32 mantissas after FP64 Gibbs
                                   energies, reaction exponents and exponent reductions

@@ -471,6 +471,16 @@ __device__ __forceinline__ float flux_diff(const MarchParamsM &P, const float *a
   }
   return acc.x + acc.y;
 }
+// flux_diff with the face products given: dw = M dd and w0 (the left face's w)
+__device__ __forceinline__ float flux_diff_w(const float *a, const float *dw, const float *w0) {
+  float2 acc = make_float2(0.0f, 0.0f);
+#pragma unroll
+  for (int t = 0; t < 8; t += 2) {
+    acc = __ffma2_rn(make_float2(a[1 + t], a[2 + t]), make_float2(dw[t], dw[t + 1]), acc);
+    acc = __ffma2_rn(make_float2(a[1 + t] - a[t], a[2 + t] - a[1 + t]), make_float2(w0[t], w0[t + 1]), acc);
+  }
+  return acc.x + acc.y;
+}
 // sum_{n != 3} v[n] (x[o+n] - x[o+3])
 __device__ __forceinline__ float dp(const float *v, const f2 *x, int o) {
   float d[8];
@@ -544,9 +554,13 @@ __device__ __forceinline__ f2 flux_E(const Win &x, int r) {
 }  // namespace m2
 
 // CH: cells per chunk; MINB: resident blocks per SM the register budget is
-// sized for (3: 168 registers, 4: 128).  The four per-cell arrays live in
-// dynamic shared memory, 4 CH M2_NT floats.
-template <int DIR, int CH, int MINB>
+// sized for (3: 168 registers, 2: 255).  The four per-cell arrays live in
+// dynamic shared memory, 4 CH M2_NT floats.  WP: the pressure products of
+// every cell's two faces (w of the left face, and w_right - w_left) are
+// formed once in the heat pass and kept in shared memory (16 CH M2_NT more
+// floats) for every species' pressure term, instead of formed again per
+// species.
+template <int DIR, int CH, int MINB, bool WP>
 __global__ void __launch_bounds__(M2_NT, MINB) k_march_m2(const DevState s, const MarchParamsM P,
                                                           float *__restrict__ dUf, int first) {
   using namespace m2;
@@ -555,6 +569,7 @@ __global__ void __launch_bounds__(M2_NT, MINB) k_march_m2(const DevState s, cons
   float(*sV)[M2_NT] = sE + CH;
   float(*sN)[M2_NT] = sV + CH;
   float(*sO)[M2_NT] = sN + CH;
+  float(*sW)[M2_NT] = sO + CH;     // [(cell * 16 + m)][thread], WP only
   const int tid = threadIdx.x;
   constexpr int E_ = (DIR + 1) % 3, F_ = (DIR + 2) % 3;
   const int ns = s.ns, mode = s.opt.mode, ref = s.opt.ref;
@@ -660,6 +675,16 @@ __global__ void __launch_bounds__(M2_NT, MINB) k_march_m2(const DevState s, cons
         // the pressure part of the correction velocity,
         // V_c,d = -(sum_l rhoD_l X_l,d + (sum_l B_l) p_d): p is in this pass's window
         if (pass == 1 && mode == 0) sV[c][tid] = -x.s(PM_SB, c) * Dp(P, f);
+        if (WP && pass == 1) {
+          float dd[8], dw[8];
+          ddiffs(f, dd);
+          mvd(P, dd, dw);
+#pragma unroll
+          for (int m = 0; m < 8; ++m) {
+            sW[c * 16 + m][tid] = w[m];
+            sW[c * 16 + 8 + m][tid] = dw[m];
+          }
+        }
         mv(P, f, 1, w);
         const float H2 = ds(a, 1, w);
         sE[c][tid] += H2 - H;
@@ -790,27 +815,41 @@ __global__ void __launch_bounds__(M2_NT, MINB) k_march_m2(const DevState s, cons
       float B[9];
 #pragma unroll
       for (int i = 0; i < 9; ++i) {
-        p[i] = x.p(PM_P, i - 4);
+        if (!WP) p[i] = x.p(PM_P, i - 4);
         B[i] = x.s(pmB(ns, k), i - 4);
         Fk[i] = mul(x.p(pmRY(ns, k), i - 4), x.p(PM_U + 2 * DIR, i - 4));
         if (mode == 0) Yk[i] = x.p(pmY(ns, k), i - 4);
       }
       float w[8];
-      mv(P, p, 0, w);
+      if (!WP) mv(P, p, 0, w);
 #pragma unroll 1
       for (int c = 0; c < n; ++c) {
         float o = -Dp(P, Fk);
         if (mode == 0) o = fmaf(Dp(P, Yk), sV[c][tid], o);
         if (narrow) {
-          const float N = flux_diff(P, B, p, w);
-          mv(P, p, 1, w);
+          float N;
+          if (WP) {
+            float w0[8], dw[8];
+#pragma unroll
+            for (int m = 0; m < 8; ++m) {
+              w0[m] = sW[c * 16 + m][tid];
+              dw[m] = sW[c * 16 + 8 + m][tid];
+            }
+            N = flux_diff_w(B, dw, w0);
+          } else {
+            N = flux_diff(P, B, p, w);
+            mv(P, p, 1, w);
+          }
           o += N;
           sN[c][tid] += N;
         }
         put(dUf, NI, 5 + k, ib + (long long)c * L.si, o, false);
         if (c + 1 < n) {
-          slide(p); slide(B); slide(Fk);
-          p[8] = x.p(PM_P, c + 5);
+          slide(B); slide(Fk);
+          if (!WP) {
+            slide(p);
+            p[8] = x.p(PM_P, c + 5);
+          }
           B[8] = x.s(pmB(ns, k), c + 5);
           Fk[8] = mul(x.p(pmRY(ns, k), c + 5), x.p(PM_U + 2 * DIR, c + 5));
           if (mode == 0) {
@@ -846,29 +885,32 @@ __global__ void __launch_bounds__(M2_NT, MINB) k_march_m2(const DevState s, cons
   }
 }
 
-template <int CH, int MINB>
+template <int CH, int MINB, bool WP>
 static void launch_m2_variant(const DevState &s, int dir, const MarchParamsM &P, float *dUf,
                               int first, int blocks, cudaStream_t st) {
-  const size_t smem = 4 * CH * M2_NT * sizeof(float);
+  const size_t smem = (4 * CH + (WP ? 16 * CH : 0)) * M2_NT * sizeof(float);
   // the attribute is per device: set it once per device and instantiation,
   // on the first (eager) launch, before any stream capture
   static bool attr_set[64] = {};
   int dev = 0;
   cudaGetDevice(&dev);
   if (dev >= 0 && dev < 64 && !attr_set[dev]) {
-    cudaFuncSetAttribute(k_march_m2<0, CH, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaFuncSetAttribute(k_march_m2<1, CH, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaFuncSetAttribute(k_march_m2<2, CH, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(k_march_m2<0, CH, MINB, WP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem);
+    cudaFuncSetAttribute(k_march_m2<1, CH, MINB, WP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem);
+    cudaFuncSetAttribute(k_march_m2<2, CH, MINB, WP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem);
     attr_set[dev] = true;
   }
   if (s.opt.persistent) {
     static int cache[64] = {};
-    const int r = resident_blocks(k_march_m2<1, CH, MINB>, M2_NT, smem, cache);
+    const int r = resident_blocks(k_march_m2<1, CH, MINB, WP>, M2_NT, smem, cache);
     if (blocks > r) blocks = r;
   }
-  if (dir == 0) k_march_m2<0, CH, MINB><<<blocks, M2_NT, smem, st>>>(s, P, dUf, first);
-  else if (dir == 1) k_march_m2<1, CH, MINB><<<blocks, M2_NT, smem, st>>>(s, P, dUf, first);
-  else k_march_m2<2, CH, MINB><<<blocks, M2_NT, smem, st>>>(s, P, dUf, first);
+  if (dir == 0) k_march_m2<0, CH, MINB, WP><<<blocks, M2_NT, smem, st>>>(s, P, dUf, first);
+  else if (dir == 1) k_march_m2<1, CH, MINB, WP><<<blocks, M2_NT, smem, st>>>(s, P, dUf, first);
+  else k_march_m2<2, CH, MINB, WP><<<blocks, M2_NT, smem, st>>>(s, P, dUf, first);
 }
 
 void launch_march_m2(const DevState &s, int dir, float *dUf, int first, int variant,
@@ -882,9 +924,9 @@ void launch_march_m2(const DevState &s, int dir, float *dUf, int first, int vari
   const long long n = s.nlines[dir];
   if (n == 0) return;
   const int blocks = (int)((n + M2_NT - 1) / M2_NT);
-  if (variant == 2) launch_m2_variant<32, 3>(s, dir, P, dUf, first, blocks, st);
-  else if (variant == 3) launch_m2_variant<16, 4>(s, dir, P, dUf, first, blocks, st);
-  else launch_m2_variant<16, 3>(s, dir, P, dUf, first, blocks, st);
+  if (variant == 2) launch_m2_variant<32, 3, false>(s, dir, P, dUf, first, blocks, st);
+  else if (variant == 3) launch_m2_variant<8, 2, true>(s, dir, P, dUf, first, blocks, st);
+  else launch_m2_variant<16, 3, false>(s, dir, P, dUf, first, blocks, st);
 }
 
 }  // namespace smc
