@@ -51,6 +51,7 @@ struct smc_handle {
   long long *d_imap = nullptr;
   long long *d_halo_dst = nullptr, *d_halo_src = nullptr;   // ghost cell -> its periodic image
   long long nhalo = 0;
+  int warm_T = 0;                 // the mixed Q planes hold an earlier evaluation's temperatures
   LineItem *d_lines[3] = {nullptr, nullptr, nullptr};
   long long nlines[3] = {0, 0, 0};
   LineItem *d_lines_xt = nullptr;       // x lines in the x-slowest (transposed) layout
@@ -199,6 +200,7 @@ DevState state(smc_handle *h) {
   s.halo_dst = h->d_halo_dst;
   s.halo_src = h->d_halo_src;
   s.nhalo = h->nhalo;
+  s.warm_T = h->precision == 1 ? h->warm_T : 0;
   return s;
 }
 
@@ -365,6 +367,7 @@ smc_status eval_rhs(smc_handle *h, const double *U, double *F, int transport, in
     Timed t(h, SMC_K_PRIM);
     if (mixed) {
       launch_prim_m(s, U, h->stream);
+      h->warm_T = 1;
     } else {
       launch_prim_interior(s, U, h->stream);
       launch_halo(s, nQ(h->ns), 8, h->stream);
@@ -1313,6 +1316,7 @@ smc_status smc_set_option(smc_handle *h, int key, double v) {
   switch (key) {
     case SMC_OPT_PRECISION:
       if (v != 0.0 && v != 1.0) return fail(h, SMC_ERR_ARG, "precision must be 0 or 1");
+      if ((int)v != h->precision) h->warm_T = 0;   // the scratch planes change meaning
       h->precision = (int)v;
       return SMC_OK;
     case SMC_OPT_M47: h->m47 = v; build_coef(h); return SMC_OK;

@@ -85,13 +85,18 @@ __device__ __forceinline__ double gRT_W(const Mech &m, int k, double T, double i
 //   e(T) = sum_j H_j T^j - T sum_k Y_k R/W_k,   H_j = sum_k Y_k (R/W_k) hT[k][j],
 // so every iteration costs one Horner evaluation of e and of de/dT = c_v.
 // Returns false if maxit steps did not converge.
+// With rho_scale != 0, Y holds rho Y_k and the mass fractions are formed as
+// Y[k] * rho_scale on the fly (the same roundings as a Y array made first,
+// without keeping that array).
 __device__ __forceinline__ bool newton_T(const Mech &m, const double *Y, double e, double T0,
                                          double tol, int maxit, double &Tout,
-                                         double *cp_mix = nullptr, double *h_mix = nullptr) {
+                                         double *cp_mix = nullptr, double *h_mix = nullptr,
+                                         double rho_scale = 0.0) {
   const int ns = m.ns;
   double H0 = 0.0, H1 = 0.0, H2 = 0.0, H3 = 0.0, H4 = 0.0, H5 = 0.0, yr_sum = 0.0;
   for (int k = 0; k < ns; ++k) {
-    const double yr = Y[k] * m.Ru_W[k];
+    const double yk = rho_scale != 0.0 ? Y[k] * rho_scale : Y[k];
+    const double yr = yk * m.Ru_W[k];
     const double *c = m.hT[k];
     H0 += yr * c[0];
     H1 += yr * c[1];

@@ -100,8 +100,17 @@ __global__ void __launch_bounds__(128) k_prim_m(const DevState s, const double *
     double Y[SMC_MAX_NS];
     for (int k = 0; k < ns; ++k) Y[k] = U[(5 + k) * NI + src] * invrho;
     const double e = rhoE * invrho - 0.5 * (u * u + v * v + w * w);
+    // first guess: this cell's temperature from the handle's previous mixed
+    // evaluation when there is one (a nearby state: two Newton steps instead
+    // of four or five from the fixed guess), else the fixed guess
+    double T0 = s.opt.T0;
+    if (INTERIOR && s.warm_T) {
+      const f2 tp = get_pair(Qf, NG, PM_T, g);
+      const double tg = (double)tp.h + (double)tp.l;
+      if (tg > 0.0 && isfinite(tg)) T0 = tg;
+    }
     double T, cpd, hm;
-    const bool ok = newton_T(m, Y, e, s.opt.T0, s.opt.tol, s.opt.maxit, T, &cpd, &hm);
+    const bool ok = newton_T(m, Y, e, T0, s.opt.tol, s.opt.maxit, T, &cpd, &hm);
     unsigned flag = 0;
     if (!ok) flag |= ST_NONCONV;
     if (!(rho > 0.0) || !(T > 0.0)) flag |= ST_NONPHYS;

@@ -43,18 +43,17 @@ __device__ __forceinline__ bool cell_reactions(const DevState &s, const double *
   const double rho = Uc[0];
   const double invrho = 1.0 / rho;
   const double u = Uc[1] * invrho, v = Uc[2] * invrho, w = Uc[3] * invrho;
-  double Y[SMC_MAX_NS];
-  for (int k = 0; k < ns; ++k) Y[k] = Uc[5 + k] * invrho;
   const double e = Uc[4] * invrho - 0.5 * (u * u + v * v + w * w);
   double T;
-  const bool ok = newton_T(m, Y, e, Tg, s.opt.tol, s.opt.maxit, T);
+  // mass fractions Uc[5 + k] / rho formed inside the solve (no Y array)
+  const bool ok = newton_T(m, Uc + 5, e, Tg, s.opt.tol, s.opt.maxit, T, nullptr, nullptr, invrho);
   if (ok) Tg = T;
   if (!ok) flag |= ST_NONCONV;
   if (!(rho > 0.0) || !(T > 0.0)) flag |= ST_NONPHYS;
   if (!isfinite(rho) || !isfinite(T)) flag |= ST_NONFINITE;
   if (s.opt.reactions && m.nr > 0) {
     if (MIX) production_rates_m(m, s.rx, T, Uc + 5, f2);
-    else production_rates(m, s.rx, rho, T, Y, f2, Uc + 5);
+    else production_rates(m, s.rx, rho, T, nullptr, f2, Uc + 5);
   } else {
     for (int k = 0; k < ns; ++k) f2[k] = 0.0;
   }

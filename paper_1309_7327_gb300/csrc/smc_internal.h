@@ -174,6 +174,8 @@ struct DevState {
   const long long *halo_dst;      // ghost cells (ghosted index) ...
   const long long *halo_src;      // ... and the ghosted index of their periodic image
   long long nhalo;                // 0: primitives are evaluated at every ghosted cell
+  int warm_T;                     // 1: the mixed primitive planes hold the temperatures of an
+                                  //    earlier evaluation (first guess of the Newton solve)
 };
 
 // Boundary-lowered x-direction terms at the cells next to the x ends; they

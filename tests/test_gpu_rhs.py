@@ -243,4 +243,9 @@ def test_tile_choices_give_identical_results_and_autotune(smc, precision):
         F = torch.empty_like(dev(U))
         h.rhs(dev(U), F)
         h.synchronize()
-    assert np.array_equal(F.cpu().numpy(), ref[choice["march"]])
+    if precision:
+        # the tuned handle's mixed temperature solve starts from the previous
+        # evaluation's temperature: the same root to the Newton tolerance
+        assert relerr(F.cpu().numpy(), ref[choice["march"]]).max() < 1e-9
+    else:
+        assert np.array_equal(F.cpu().numpy(), ref[choice["march"]])
