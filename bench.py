@@ -252,18 +252,18 @@ _CHAIN_SRC = ["kernels_sdc.cu", "chem.cuh", "smc_internal.h"]
 _MARCH_SRC = ["kernels_rhs.cu", "bc.cuh", "chem.cuh", "smc_internal.h"]
 NCU_TRAFFIC = {
     # c4 at n = 64 (780 045 cells, state 162 MB > L2), the eight chain launches
-    # of one step (four sweeps x two coarse intervals): mean 18 881 B per cell
+    # of one step (four sweeps x two coarse intervals): mean 17 714 B per cell
     # and launch (profiles/k_fine_chain_fp64_c4_n64.md).  The same kernel
     # runs in both precisions (FP64 rates).
-    ("k_fine_chain", "fp64", "c4"): {"bytes_per_cell": 18881.0, "files": _CHAIN_SRC,
-                                     "digest": "8770825bb6ed6ee5"},
-    ("k_fine_chain", "mixed", "c4"): {"bytes_per_cell": 18881.0, "files": _CHAIN_SRC,
-                                      "digest": "8770825bb6ed6ee5"},
+    ("k_fine_chain", "fp64", "c4"): {"bytes_per_cell": 17714.0, "files": _CHAIN_SRC,
+                                     "digest": "36f134559e7d13c9"},
+    ("k_fine_chain", "mixed", "c4"): {"bytes_per_cell": 17714.0, "files": _CHAIN_SRC,
+                                      "digest": "36f134559e7d13c9"},
     # the per-face FP64 line kernel, x / y / z launches of one evaluation at
-    # n = 64: 25.68 / 12.84 / 11.88 GB, mean 21 538 B per cell and launch
+    # n = 64: 25.69 / 12.31 / 12.00 GB, mean 21 352 B per cell and launch
     # (profiles/k_march_fp64_c4_n64.md)
-    ("k_march", "fp64", "c4"): {"bytes_per_cell": 21538.0, "files": _MARCH_SRC,
-                                "digest": "cb2ea9f86c012bca"},
+    ("k_march", "fp64", "c4"): {"bytes_per_cell": 21352.0, "files": _MARCH_SRC,
+                                "digest": "a2de9dcdcc89a736"},
 }
 
 
