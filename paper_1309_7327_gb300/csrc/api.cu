@@ -372,6 +372,8 @@ smc_status eval_rhs(smc_handle *h, const double *U, double *F, int transport, in
       launch_prim_interior(s, U, h->stream);
       launch_halo(s, nQ(h->ns), 8, h->stream);
     }
+    // the ghost-cell copy is a second launch of this class
+    if (s.nhalo > 0) h->launches[SMC_K_PRIM]++;
   }
   if (transport) {
     {

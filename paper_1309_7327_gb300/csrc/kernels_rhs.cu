@@ -292,7 +292,7 @@ __device__ __forceinline__ void face_fluxes(const DevState &s, const MarchParams
 }
 
 template <int DIR>
-__global__ void __launch_bounds__(128) k_march(const DevState s, const MarchParams P,
+__global__ void __launch_bounds__(128, 3) k_march(const DevState s, const MarchParams P,
                                                double *__restrict__ dU, int first) {
   const long long item = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (item >= s.nlines[DIR]) return;
