@@ -174,12 +174,20 @@ enum {
   SMC_OPT_BDF_ATOL = 21,       /* absolute tolerance of the implicit reaction integration in
                                   mass-fraction units (the weight of rho Y_k is
                                   atol rho + rtol |rho Y_k|), >= 0, default 1e-12 */
-  SMC_OPT_PERSISTENT = 22      /* launch shape of the multirate reaction chain and the
+  SMC_OPT_PERSISTENT = 22,     /* launch shape of the multirate reaction chain and the
                                   sliding-window line kernels: 0 (default) one thread per cell
                                   or line segment, as many blocks as that takes; 1 one grid of
                                   the device's resident capacity (blocks per SM from the
                                   occupancy calculator x SM count) whose threads loop over the
                                   work items, so no partly filled last wave of blocks */
+  SMC_OPT_ALU = 23             /* FP64 rate arithmetic moved to the integer and FP32 pipes
+                                  (the FP64 pipe is the scarce one): 0 none; 1 (default) the
+                                  exponentials of the production rates, the transport power law
+                                  and the implicit integrator (smc_exp variant 1; within 2 ulp
+                                  like variant 0); 2 also the products of the rate terms and of
+                                  the temperature solve (smc_dmul: correctly rounded, the FP64
+                                  unit's results bit for bit, but slower: the 64-bit integer
+                                  multiplies cost more issue slots than they free) */
 };
 
 /* Kernel classes counted in smc_stats (launches always; times only while
@@ -345,13 +353,24 @@ smc_status smc_heat2d(int N, double h, const double *a, const double *b, const d
                       double m47, double m48, double t0, double dt, int nsteps, int nodes,
                       int sweeps, double *u, long long *n_evals, void *stream);
 
-/* The exponential used by the production rates (a table-driven method, not
+/* The exponentials used by the production rates (table-driven methods, not
  * the paper's: Sec. 2.1 only needs exp), applied elementwise y[i] = exp(x[i])
- * on the device for accuracy tests.  x and y are caller-owned device arrays
- * of n doubles (n >= 0).  Arguments with |x| >= 512 are clamped to
- * [-708, 709].  Synchronous; returns SMC_ERR_ARG for null arrays or
- * host pointers, SMC_ERR_CUDA if the launch fails. */
-smc_status smc_exp(const double *x, double *y, long long n);
+ * on the device for accuracy tests.  variant 0: the table method in FP64
+ * arithmetic; variant 1: the same decomposition with the argument reduction
+ * in 128-bit fixed point, exp(r) as a float pair and the result assembled in
+ * 64-bit fixed point (integer and FP32 pipes; SMC_OPT_ALU).  x and y are
+ * caller-owned device arrays of n doubles (n >= 0).  Arguments with
+ * |x| >= 512 are clamped to [-708, 709].  Synchronous; returns SMC_ERR_ARG
+ * for null arrays, host pointers or another variant, SMC_ERR_CUDA if the
+ * launch fails. */
+smc_status smc_exp(const double *x, double *y, long long n, int variant);
+
+/* y[i] = a[i] * b[i] by the integer-pipe product the production rates use
+ * under SMC_OPT_ALU = 2 (the 106-bit product of the significands, rounded to
+ * nearest even), for its exactness test against the FP64 product.  Device
+ * arrays of n doubles; synchronous; SMC_ERR_ARG for null or host arrays,
+ * SMC_ERR_CUDA if the launch fails. */
+smc_status smc_dmul(const double *a, const double *b, double *y, long long n);
 
 /* Implicit integration of the reactions alone, cell by cell (the coarse
  * reaction term of MRSDC mode 2, eq. mrupdate2):

@@ -1366,6 +1366,17 @@ smc_status smc_set_option(smc_handle *h, int key, double v) {
       if (v != 0.0 && v != 1.0) return fail(h, SMC_ERR_ARG, "persistent must be 0 or 1");
       h->opt.persistent = (int)v;
       return SMC_OK;
+    case SMC_OPT_ALU: {
+      if (v != 0.0 && v != 1.0 && v != 2.0) return fail(h, SMC_ERR_ARG, "alu must be 0, 1 or 2");
+      // the flag lives in the device copy of the mechanism: update it in
+      // stream order, after the work already queued
+      h->hmech.alu = (int)v;
+      CUDA_TRY(h, cudaMemcpyAsync(reinterpret_cast<char *>(h->d_mech) + offsetof(Mech, alu),
+                                  &h->hmech.alu, sizeof(int), cudaMemcpyHostToDevice,
+                                  h->stream));
+      CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+      return SMC_OK;
+    }
     case SMC_OPT_SDC_EXIT:
       if (!(v >= 0.0) || !std::isfinite(v)) return fail(h, SMC_ERR_ARG, "sdc exit must be >= 0");
       h->sdc_exit = v;
@@ -1580,8 +1591,8 @@ smc_status smc_react_integrate(smc_handle *h, const double *U, const double *G, 
   return SMC_OK;
 }
 
-smc_status smc_exp(const double *x, double *y, long long n) {
-  if (n < 0 || (n > 0 && (!x || !y))) return SMC_ERR_ARG;
+smc_status smc_exp(const double *x, double *y, long long n, int variant) {
+  if (n < 0 || (n > 0 && (!x || !y)) || (variant != 0 && variant != 1)) return SMC_ERR_ARG;
   if (n == 0) return SMC_OK;
   if (!is_device_ptr(x) || !is_device_ptr(y)) return SMC_ERR_ARG;
   Mech *hm = new Mech();
@@ -1595,12 +1606,22 @@ smc_status smc_exp(const double *x, double *y, long long n) {
     return SMC_ERR_CUDA;
   }
   if (cudaMemcpy(dm, hm, sizeof(Mech), cudaMemcpyHostToDevice) != cudaSuccess) st = SMC_ERR_CUDA;
-  if (!st) launch_exp(dm, x, y, n, 0);
+  if (!st) launch_exp(dm, x, y, n, variant, 0);
   if (!st && (cudaGetLastError() != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess))
     st = SMC_ERR_CUDA;
   cudaFree(dm);
   delete hm;
   return st;
+}
+
+smc_status smc_dmul(const double *a, const double *b, double *y, long long n) {
+  if (n < 0 || (n > 0 && (!a || !b || !y))) return SMC_ERR_ARG;
+  if (n == 0) return SMC_OK;
+  if (!is_device_ptr(a) || !is_device_ptr(b) || !is_device_ptr(y)) return SMC_ERR_ARG;
+  launch_dmul(a, b, y, n, 0);
+  if (cudaGetLastError() != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess)
+    return SMC_ERR_CUDA;
+  return SMC_OK;
 }
 
 const char *smc_last_error(smc_handle *h) {

@@ -52,6 +52,141 @@ __device__ __forceinline__ double fast_exp(const Mech &m, double x) {
   return __hiloint2double(__double2hiint(y) + (k << 20), __double2loint(y));
 }
 
+// exp(x) to the accuracy of fast_exp without FP64 arithmetic on its main
+// path.  On this GPU the FP64 pipe issues one operation for every 64 of the
+// FP32 pipe, and exponentials are a third of the FP64 operations of the
+// production rates; here every step runs on the integer and FP32 pipes.  The
+// decomposition is fast_exp's, x = (2048 k + j) ln2/2048 + r:
+//  * t = x 2048/ln2 in 64-bit fixed point: x's 53-bit significand times
+//    2048/ln2 held to 128 bits (CI + CR 2^-64, both scaled by 2^52), so that
+//    n = round(t) and u = t - n carry no rounding error that matters
+//    (|t| < 2^22 for the clamped range);
+//  * r = u ln2/2048 and exp(r) - 1 = r + r^2/2 + r^3/6 + r^4/24 as a float
+//    pair (hi + lo); |r| <= ln2/4096, so the pair's ~46 bits are far below
+//    the double rounding of the result and the omitted r^5/120 < 2e-21;
+//  * exp(x) = 2^k T_j (1 + p): T_j = 2^(j/2048) from the FP64 table, the sum
+//    T_j + T_j p formed in 64-bit fixed point (2^62 scale) and rounded once
+//    to 53 bits, 2^k added to the exponent field.
+// |x| < 2^-20 is left to fast_exp (the fixed point would keep too few bits
+// of so small a t); |x| >= 512, infinities and NaN are clamped or passed as
+// in fast_exp.  Error within about 1 ulp.
+__device__ __forceinline__ double exp_alu(const Mech &m, double x) {
+  long long b = __double_as_longlong(x);
+  int ef = (int)((b >> 52) & 0x7ff);
+  if (ef < 1023 - 20) return fast_exp(m, x);
+  if (ef >= 1023 + 9) {
+    if (x != x) return x;
+    if (x > 709.0) x = 709.0;
+    if (x < -708.0) x = -708.0;
+    b = __double_as_longlong(x);
+    ef = (int)((b >> 52) & 0x7ff);
+  }
+  // |x| = M 2^(ef - 1075), 2048/ln2 = (CI + CR 2^-64) 2^-52, so
+  // t 2^64 = M (CI + CR 2^-64) 2^(ef - 1063); s = 1063 - ef is in 31..60
+  const unsigned long long CI = 0xb8aa3b295c17f0bbULL, CR = 0xbe87fed0691d3e88ULL;
+  const unsigned long long M = ((unsigned long long)b & 0xFFFFFFFFFFFFFULL) | (1ULL << 52);
+  const int s = 1063 - ef;
+  const unsigned long long ph = __umul64hi(M, CI), pl = M * CI;
+  const unsigned long long corr = __umul64hi(M, CR) >> s;
+  unsigned long long ip = ph >> s;
+  unsigned long long fr = (pl >> s) | (ph << (64 - s));
+  const unsigned long long fr2 = fr + corr;
+  ip += fr2 < fr ? 1ULL : 0ULL;
+  // round to nearest: a fraction of 1/2 or more counts as a negative u
+  const long long f = (long long)fr2;
+  const int na = (int)ip + (f < 0 ? 1 : 0);
+  // u = f 2^-64 in [-1/2, 1/2): its top 48 bits as two exact floats
+  const float u1 = (float)(int)(f >> 40) * 0x1p-24f;
+  const float u2 = (float)(int)((f >> 16) & 0xFFFFFF) * 0x1p-48f;
+  // r = u ln2/2048 with ln2/2048 = LH + LL
+  const float LH = 0x1.62e43p-12f, LL = -0x1.05c61p-40f;
+  float rh = u1 * LH;
+  float rl = fmaf(u1, LH, -rh) + fmaf(u1, LL, u2 * LH);
+  int n = na;
+  if (b < 0) {
+    n = -na;
+    rh = -rh;
+    rl = -rl;
+  }
+  // p = exp(r) - 1 as a float pair
+  const float sq = rh * rh;
+  const float sqe = fmaf(rh, rh, -sq);
+  const float h2 = 0.5f * sq;
+  const float ph2 = rh + h2;                         // |rh| > |h2|: exact error below
+  const float phe = h2 - (ph2 - rh);
+  const float c34 = sq * rh * fmaf(rh, 1.0f / 24.0f, 1.0f / 6.0f);
+  const float pl2 = phe + rl + fmaf(0.5f, sqe, rh * rl) + c34;
+  // T_j (1 + p) in fixed point, T_j = MT 2^-52 in [1, 2)
+  const int j = n & (SMC_EXP_TABLE - 1);
+  const int k = n >> 11;
+  const unsigned long long MT =
+      ((unsigned long long)__double_as_longlong(m.exp2tab[j]) & 0xFFFFFFFFFFFFFULL) | (1ULL << 52);
+  const float th = (float)(unsigned)(MT >> 29) * 0x1p-23f;
+  const float tl = (float)(unsigned)(MT & 0x1FFFFFFFULL) * 0x1p-52f;
+  const float q1 = th * ph2;
+  const float q2 = fmaf(th, ph2, -q1) + fmaf(th, pl2, tl * ph2);
+  const long long Y = (long long)(MT << 10) + __float2ll_rn(q1 * 0x1p62f) + __float2ll_rn(q2 * 0x1p62f);
+  int sh = 10, eadj = 0;
+  if (Y < (1LL << 62)) {
+    sh = 9;
+    eadj = -1;
+  }
+  unsigned long long mr = ((unsigned long long)Y + (1ULL << (sh - 1))) >> sh;
+  if (mr >> 53) {
+    mr >>= 1;
+    eadj += 1;
+  }
+  return __longlong_as_double((long long)((unsigned long long)(1023 + k + eadj) << 52) |
+                              (long long)(mr & 0xFFFFFFFFFFFFFULL));
+}
+
+// The exponential the mechanism's flag selects (SMC_OPT_ALU).
+__device__ __forceinline__ double mech_exp(const Mech &m, double x) {
+  return m.alu ? exp_alu(m, x) : fast_exp(m, x);
+}
+
+// a * b rounded to nearest (ties to even) exactly as the FP64 unit rounds it,
+// in integer arithmetic: the 106-bit product of the two 53-bit significands
+// (one shifted left by 11, so that the top word of the product holds the 52
+// or 53 leading bits), normalised, rounded once on its round and sticky bits,
+// and packed with the summed exponents.  Zero, subnormal, infinite and NaN
+// operands, and products that could leave the normal range, go to the FP64
+// unit (a * b).
+__device__ __forceinline__ double dmul_alu(double a, double b) {
+  const unsigned long long ua = (unsigned long long)__double_as_longlong(a);
+  const unsigned long long ub = (unsigned long long)__double_as_longlong(b);
+  const int ea = (int)((ua >> 52) & 0x7ff), eb = (int)((ub >> 52) & 0x7ff);
+  int e = ea + eb - 1023;
+  if ((unsigned)(ea - 1) > 2045u || (unsigned)(eb - 1) > 2045u || (unsigned)(e - 1) > 2043u)
+    return a * b;
+  const unsigned long long ma = (ua & 0xFFFFFFFFFFFFFULL) | (1ULL << 52);
+  const unsigned long long mb = (ub & 0xFFFFFFFFFFFFFULL) | (1ULL << 52);
+  const unsigned long long x = ma << 11;
+  const unsigned long long hi = __umul64hi(x, mb);     // ma mb 2^11 = hi 2^64 + lo
+  const unsigned long long lo = x * mb;
+  unsigned long long m, rest;                          // 53 result bits, the bits below them
+  if (hi >> 52) {                                      // ma mb in [2^105, 2^106)
+    m = hi;
+    rest = lo;
+    e += 1;
+  } else {                                             // ma mb in [2^104, 2^105)
+    m = (hi << 1) | (lo >> 63);
+    rest = lo << 1;
+  }
+  m += ((rest >> 63) && ((rest << 1) != 0 || (m & 1))) ? 1ULL : 0ULL;
+  if (m >> 53) {
+    m >>= 1;
+    e += 1;
+  }
+  return __longlong_as_double((long long)(((ua ^ ub) & 0x8000000000000000ULL) |
+                                          ((unsigned long long)e << 52) | (m & 0xFFFFFFFFFFFFFULL)));
+}
+
+// The product the mechanism's flag selects (SMC_OPT_ALU); both round alike.
+__device__ __forceinline__ double mech_mul(bool alu_mul, double a, double b) {
+  return alu_mul ? dmul_alu(a, b) : a * b;
+}
+
 // cp/R of species k at T.
 __device__ __forceinline__ double cpR(const Mech &m, int k, double T) {
   const double *c = m.cp[k];
@@ -93,10 +228,11 @@ __device__ __forceinline__ bool newton_T(const Mech &m, const double *Y, double 
                                          double *cp_mix = nullptr, double *h_mix = nullptr,
                                          double rho_scale = 0.0) {
   const int ns = m.ns;
+  const bool amul = m.alu >= 2;
   double H0 = 0.0, H1 = 0.0, H2 = 0.0, H3 = 0.0, H4 = 0.0, H5 = 0.0, yr_sum = 0.0;
   for (int k = 0; k < ns; ++k) {
-    const double yk = rho_scale != 0.0 ? Y[k] * rho_scale : Y[k];
-    const double yr = yk * m.Ru_W[k];
+    const double yk = rho_scale != 0.0 ? mech_mul(amul, Y[k], rho_scale) : Y[k];
+    const double yr = mech_mul(amul, yk, m.Ru_W[k]);
     const double *c = m.hT[k];
     H0 += yr * c[0];
     H1 += yr * c[1];
@@ -147,6 +283,7 @@ __device__ __forceinline__ void production_rates(const Mech &m, const Reaction *
                                                  double rho, double T, const double *Y,
                                                  double *wdot, const double *rhoY = nullptr) {
   const int ns = m.ns;
+  const bool alu = m.alu != 0, amul = m.alu >= 2;
   double z[SMC_MAX_NS], g[SMC_MAX_NS];
   const double lnT = log(T);
   const double invT = 1.0 / T;
@@ -158,11 +295,11 @@ __device__ __forceinline__ void production_rates(const Mech &m, const Reaction *
   gs *= m.inv_ns;
   for (int k = 0; k < ns; ++k) {
     g[k] -= gs;
-    z[k] = (rhoY ? rhoY[k] : rho * Y[k]) * fast_exp(m, g[k]);
+    z[k] = mech_mul(amul, rhoY ? rhoY[k] : rho * Y[k], alu ? exp_alu(m, g[k]) : fast_exp(m, g[k]));
     wdot[k] = 0.0;
   }
   // P^j for j = -3..3
-  const double P1 = T * (kRu / kPatm) * fast_exp(m, gs), Pm1 = 1.0 / P1;
+  const double P1 = T * (kRu / kPatm) * (alu ? exp_alu(m, gs) : fast_exp(m, gs)), Pm1 = 1.0 / P1;
   const double P2 = P1 * P1, Pm2 = Pm1 * Pm1;
   const double Ppow[7] = {Pm2 * Pm1, Pm2, Pm1, 1.0, P1, P2, P2 * P1};
   for (int r = 0; r < m.nr; ++r) {
@@ -170,9 +307,9 @@ __device__ __forceinline__ void production_rates(const Mech &m, const Reaction *
     double ex = fma(R.b, lnT, fma(-R.Ea_R, invT, R.lnA));
     for (int i = 0; i < R.nf; ++i) ex = fma(-R.fcd[i], g[R.fk[i]], ex);
     double fwd = z[R.fm[0]], rev = z[R.rm[0]];
-    for (int i = 1; i < R.nfm; ++i) fwd *= z[R.fm[i]];
-    for (int i = 1; i < R.nrm; ++i) rev *= z[R.rm[i]];
-    const double q = fast_exp(m, ex) * fma(-Ppow[R.dn + 3], rev, fwd);
+    for (int i = 1; i < R.nfm; ++i) fwd = mech_mul(amul, fwd, z[R.fm[i]]);
+    for (int i = 1; i < R.nrm; ++i) rev = mech_mul(amul, rev, z[R.rm[i]]);
+    const double q = mech_mul(amul, alu ? exp_alu(m, ex) : fast_exp(m, ex), fma(-Ppow[R.dn + 3], rev, fwd));
     for (int i = 0; i < R.nf; ++i) wdot[R.fk[i]] = fma(-R.fcw[i], q, wdot[R.fk[i]]);
     for (int i = 0; i < R.nr_; ++i) wdot[R.rk[i]] = fma(R.rcw[i], q, wdot[R.rk[i]]);
   }

@@ -77,7 +77,7 @@ __device__ void rates_jac(const Mech &m, const Reaction *__restrict__ rx, double
   }
   gs *= m.inv_ns;
   for (int k = 0; k < ns; ++k) {
-    E[k] = fast_exp(m, g[k] - gs);
+    E[k] = mech_exp(m, g[k] - gs);
     z[k] = y[k] * E[k];
     wdot[k] = 0.0;
   }
@@ -88,7 +88,7 @@ __device__ void rates_jac(const Mech &m, const Reaction *__restrict__ rx, double
       for (int j = 0; j < ns; ++j) J[k * NS + j] = 0.0f;
     }
   }
-  const double P1 = T * (kRu / kPatm) * fast_exp(m, gs), Pm1 = 1.0 / P1;
+  const double P1 = T * (kRu / kPatm) * mech_exp(m, gs), Pm1 = 1.0 / P1;
   const double P2 = P1 * P1, Pm2 = Pm1 * Pm1;
   const double Ppow[7] = {Pm2 * Pm1, Pm2, Pm1, 1.0, P1, P2, P2 * P1};
   const float invTf = trunc_float(invT);
@@ -99,7 +99,7 @@ __device__ void rates_jac(const Mech &m, const Reaction *__restrict__ rx, double
     double fwd = z[R.fm[0]], rev = z[R.rm[0]];
     for (int i = 1; i < R.nfm; ++i) fwd *= z[R.fm[i]];
     for (int i = 1; i < R.nrm; ++i) rev *= z[R.rm[i]];
-    const double K = fast_exp(m, ex);
+    const double K = mech_exp(m, ex);
     const double KP = K * Ppow[R.dn + 3];
     const double F = K * fwd, B = KP * rev;
     const double q = F - B;

@@ -134,7 +134,7 @@ __global__ void __launch_bounds__(128) k_prim_m(const DevState s, const double *
     // cancel (a species' gradient and pressure fluxes can be several times its
     // net flux, and a face flux tens of times its divergence), so rounding
     // noise from a chain of FP32 operations would be amplified by as much.
-    const double eta_d = m.eta_ref * fast_exp(m, m.eta_exp * log(T * m.inv_T_ref));
+    const double eta_d = m.eta_ref * mech_exp(m, m.eta_exp * log(T * m.inv_T_ref));
     const double xi_d = s.opt.xi_ratio * eta_d;
     const double rd0_d = eta_d * m.inv_Pr;           // lambda / cp = rho D_k Le_k
     const double bq = rd0_d / p;                     // B_k = bq (X_k - Y_k) / Le_k

@@ -61,7 +61,7 @@ __global__ void __launch_bounds__(128) k_prim(const DevState s, const double *__
     // eta_ref (T / T_ref)^eta_exp as exp(eta_exp ln(T / T_ref)) with the
     // library's exponential (one log and one table exponential instead of a
     // general power)
-    const double eta = m.eta_ref * fast_exp(m, m.eta_exp * log(T * m.inv_T_ref));
+    const double eta = m.eta_ref * mech_exp(m, m.eta_exp * log(T * m.inv_T_ref));
     const double xi = s.opt.xi_ratio * eta;
     const double lam = cpm * eta * m.inv_Pr;
     const double rd0 = lam / cpm;

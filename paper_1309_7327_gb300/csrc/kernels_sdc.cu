@@ -242,15 +242,29 @@ void launch_residual(const double *U0, const double *UM, const ResidualTable *ta
   k_residual<<<(int)blocks, 256, 0, st>>>(U0, UM, tab, nv, NI, out);
 }
 
+template <bool ALU>
 __global__ void __launch_bounds__(256) k_exp(const Mech *__restrict__ m, const double *__restrict__ x,
                                              double *__restrict__ y, long long n) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x)
-    y[i] = fast_exp(*m, x[i]);
+    y[i] = ALU ? exp_alu(*m, x[i]) : fast_exp(*m, x[i]);
 }
 
-void launch_exp(const Mech *m, const double *x, double *y, long long n, cudaStream_t st) {
-  k_exp<<<grid_for(n, 256), 256, 0, st>>>(m, x, y, n);
+void launch_exp(const Mech *m, const double *x, double *y, long long n, int variant,
+                cudaStream_t st) {
+  if (variant == 1) k_exp<true><<<grid_for(n, 256), 256, 0, st>>>(m, x, y, n);
+  else k_exp<false><<<grid_for(n, 256), 256, 0, st>>>(m, x, y, n);
+}
+
+__global__ void __launch_bounds__(256) k_dmul(const double *__restrict__ a, const double *__restrict__ b,
+                                              double *__restrict__ y, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    y[i] = dmul_alu(a[i], b[i]);
+}
+
+void launch_dmul(const double *a, const double *b, double *y, long long n, cudaStream_t st) {
+  k_dmul<<<grid_for(n, 256), 256, 0, st>>>(a, b, y, n);
 }
 
 // The chain's per-thread arrays (state, rates, Gibbs terms) live in local

@@ -50,6 +50,7 @@ const char *pack_mechanism(const smc_mechanism *mech, int max_reactions, Mech &M
   if (!(mech->eta_ref > 0) || !(mech->T_ref > 0) || !(mech->Pr > 0))
     return "transport parameters must be positive";
   M.inv_ns = 1.0 / ns;
+  M.alu = 1;
   for (int j = 0; j < SMC_EXP_TABLE; ++j) {
     const long double t = exp2l((long double)j / (long double)SMC_EXP_TABLE);
     M.exp2tab[j] = (double)t;

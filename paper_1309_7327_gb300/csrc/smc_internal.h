@@ -35,7 +35,9 @@ struct Mech {
                                   //   : {a6, a1 - a7 - ln W_k, -a1, -a2/2, -a3/6, -a4/12, -a5/20}
   double eta_ref, inv_T_ref, eta_exp, inv_Pr;
   double inv_ns;
-  double exp2tab[SMC_EXP_TABLE];  // 2^(j/2048) (table of fast_exp)
+  int alu;                        // rate arithmetic moved off the FP64 pipe (SMC_OPT_ALU): 1 the
+                                  // exponentials (exp_alu), 2 also the products (dmul_alu)
+  double exp2tab[SMC_EXP_TABLE];  // 2^(j/2048) (table of fast_exp and exp_alu)
   float exp2tabf[SMC_EXP_TABLE];  // the same rounded to float (mixed-precision rates)
   // float copies for the mixed-precision transport (no conversions in kernels)
   float hTf[SMC_MAX_NS][6];
@@ -262,7 +264,9 @@ struct FineChain {
 void launch_fine_chain(const DevState &s, const double *U0, double *U, const FineChain &fc,
                        cudaStream_t st);
 void launch_chem_only(const DevState &s, const double *U, double *F2, cudaStream_t st);
-void launch_exp(const Mech *m, const double *x, double *y, long long n, cudaStream_t st);
+void launch_exp(const Mech *m, const double *x, double *y, long long n, int variant,
+                cudaStream_t st);
+void launch_dmul(const double *a, const double *b, double *y, long long n, cudaStream_t st);
 
 // Implicit reaction integration over one coarse interval (MRSDC mode 2,
 // kernels_bdf.cu): per cell, dU/dtau = R(U) + G on [0, dtp] by the BDF

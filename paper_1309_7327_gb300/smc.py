@@ -29,13 +29,13 @@ OPT = dict(precision=0, m47=1, m48=2, diffusion_mode=3, ref_species=4, xi_ratio=
            newton_tol=6, newton_maxit=7, t_guess=8, reactions=9, segment=10, profile=11,
            use_graphs=12, x_layout=13, march=14, rates=15,
            fine_repeat=16, sdc_exit=17, chain_blocks=18, mr_mode=19, bdf_rtol=20, bdf_atol=21,
-           persistent=22)
+           persistent=22, alu=23)
 KERNELS = ["prim", "grad", "march", "final", "update", "fine", "chem", "other", "bdf"]
 
 EXPORTS = ["smc_create", "smc_destroy", "smc_rhs", "smc_sdc_step", "smc_prim_to_cons", "smc_autotune",
            "smc_set_stream", "smc_set_option", "smc_get_stats", "smc_synchronize",
            "smc_invalidate", "smc_collocation", "smc_multirate_collocation", "smc_rhs_noalloc",
-           "smc_exp", "smc_heat2d", "smc_react_integrate", "smc_fma_throughput",
+           "smc_exp", "smc_dmul", "smc_heat2d", "smc_react_integrate", "smc_fma_throughput",
            "smc_last_error"]
 
 
@@ -94,7 +94,9 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
     lib.smc_multirate_collocation.argtypes = [C.c_int, C.c_int, C.c_int, vp, vp, vp, vp]
     lib.smc_heat2d.argtypes = [C.c_int, dp, vp, vp, vp, dp, dp, dp, dp, C.c_int, C.c_int, C.c_int,
                                vp, C.POINTER(C.c_longlong), vp]
-    lib.smc_exp.argtypes = [vp, vp, C.c_longlong]
+    lib.smc_exp.argtypes = [vp, vp, C.c_longlong, C.c_int]
+    lib.smc_dmul.argtypes = [vp, vp, vp, C.c_longlong]
+    lib.smc_dmul.restype = C.c_int
     lib.smc_react_integrate.argtypes = [vp, vp, vp, dp, vp]
     lib.smc_exp.restype = C.c_int
     lib.smc_rhs_noalloc.argtypes = [C.POINTER(C.c_int), C.POINTER(C.c_double),
@@ -180,12 +182,24 @@ def smc_heat2d(N, h, a, b, G, u, t0, dt, nsteps, m47=3557.0 / 44100.0, m48=-2083
     return ev.value
 
 
-def smc_exp(x, y):
-    """y = exp(x) elementwise by the library's exponential (CUDA float64
-    tensors of equal size); synchronous."""
+def smc_dmul(a, b, y):
+    """y = a * b elementwise by the library's integer-pipe product (CUDA
+    float64 tensors of equal size); synchronous."""
+    if not (a.numel() == b.numel() <= y.numel()):
+        raise ValueError("a, b and y must have the same size")
+    st = lib().smc_dmul(_ptr(a), _ptr(b), _ptr(y), C.c_longlong(a.numel()))
+    if st != SMC_OK:
+        raise SmcError(st, "smc_dmul")
+    return y
+
+
+def smc_exp(x, y, variant=0):
+    """y = exp(x) elementwise by one of the library's exponentials (CUDA
+    float64 tensors of equal size): 0 the FP64 table method, 1 the integer /
+    FP32 one; synchronous."""
     if y.numel() < x.numel():
         raise ValueError("y is smaller than x")
-    st = lib().smc_exp(_ptr(x), _ptr(y), C.c_longlong(x.numel()))
+    st = lib().smc_exp(_ptr(x), _ptr(y), C.c_longlong(x.numel()), int(variant))
     if st != SMC_OK:
         raise SmcError(st, "smc_exp")
     return y
