@@ -177,16 +177,25 @@ def march_flops_per_cell_mixed(ns: int, mode: int = 0) -> float:
     return face + diffs + conv + vc + 5 + ns
 
 
-def chem_flops_per_eval(ns: int, nr: int) -> float:
+EXP_FLOPS = 14.0      # FP64 flops of one table-driven exponential in FP64 arithmetic
+
+
+def chem_flops_per_eval(ns: int, nr: int, alu: int = 1) -> float:
     """FP64 flops of one reaction-term evaluation per cell (FMA = 2), counted
     from the source: per reaction 34 (exponent 7.6, concentration products
     2.5, table-driven exponential 14, net rate 3, species updates 7.2), per
     species 43 (Gibbs energy 12, shift 2, z_k with its exponential 15,
     mixture polynomial of the Newton solve 14), per cell 210 (ln T, 1/T,
-    the pressure powers, 1/rho, velocities, the Newton iterations).
-    Cross-checked with ncu's DFMA/DMUL/DADD counts of k_fine_chain (4132 per
-    evaluation at 21 species / 84 reactions against 3969 counted)."""
-    return 34.0 * nr + 43.0 * ns + 210.0
+    the pressure powers with their exponential, 1/rho, velocities, the
+    Newton iterations).  Cross-checked with ncu's DFMA/DMUL/DADD counts of
+    k_fine_chain (4132 per evaluation at 21 species / 84 reactions against
+    3969 counted).  alu >= 1 (SMC_OPT_ALU, the default): the exponentials,
+    one per reaction, per species and per cell, run on the integer and FP32
+    pipes, and the count is that of the FP64 pipe (14 flops less each)."""
+    flops = 34.0 * nr + 43.0 * ns + 210.0
+    if alu:
+        flops -= EXP_FLOPS * (nr + ns + 1)
+    return flops
 
 
 def chem_flops_per_eval_rates32(ns: int, nr: int) -> float:
@@ -197,12 +206,13 @@ def chem_flops_per_eval_rates32(ns: int, nr: int) -> float:
     return 12.6 * nr + 33.0 * ns + 200.0
 
 
-def fine_flops_per_substep(ns: int, nr: int, M1: int, Y: int, rates32: bool = False) -> float:
+def fine_flops_per_substep(ns: int, nr: int, M1: int, Y: int, rates32: bool = False,
+                           alu: int = 1) -> float:
     """FP64 flops of one fine substep of the multirate chain per cell: one
     reaction-term evaluation (Newton solve included) and the update of
     eq. mrupdate, NV (2 + 2 (M1 + 1)) + ns (2 + 2 Y)."""
     nv = 5 + ns
-    chem = chem_flops_per_eval_rates32(ns, nr) if rates32 else chem_flops_per_eval(ns, nr)
+    chem = chem_flops_per_eval_rates32(ns, nr) if rates32 else chem_flops_per_eval(ns, nr, alu)
     return chem + nv * (2 + 2 * (M1 + 1)) + ns * (2 + 2 * Y)
 
 
@@ -252,18 +262,18 @@ _CHAIN_SRC = ["kernels_sdc.cu", "chem.cuh", "smc_internal.h"]
 _MARCH_SRC = ["kernels_rhs.cu", "bc.cuh", "chem.cuh", "smc_internal.h"]
 NCU_TRAFFIC = {
     # c4 at n = 64 (780 045 cells, state 162 MB > L2), the eight chain launches
-    # of one step (four sweeps x two coarse intervals): mean 17 714 B per cell
+    # of one step (four sweeps x two coarse intervals): mean 17 620 B per cell
     # and launch (profiles/k_fine_chain_fp64_c4_n64.md).  The same kernel
     # runs in both precisions (FP64 rates).
-    ("k_fine_chain", "fp64", "c4"): {"bytes_per_cell": 17714.0, "files": _CHAIN_SRC,
-                                     "digest": "36f134559e7d13c9"},
-    ("k_fine_chain", "mixed", "c4"): {"bytes_per_cell": 17714.0, "files": _CHAIN_SRC,
-                                      "digest": "36f134559e7d13c9"},
+    ("k_fine_chain", "fp64", "c4"): {"bytes_per_cell": 17620.0, "files": _CHAIN_SRC,
+                                     "digest": "3a39d7696856463d"},
+    ("k_fine_chain", "mixed", "c4"): {"bytes_per_cell": 17620.0, "files": _CHAIN_SRC,
+                                      "digest": "3a39d7696856463d"},
     # the per-face FP64 line kernel, x / y / z launches of one evaluation at
-    # n = 64: 25.71 / 12.96 / 12.04 GB, mean 21 669 B per cell and launch
+    # n = 64: 25.72 / 12.95 / 12.03 GB, mean 21 663 B per cell and launch
     # (profiles/k_march_fp64_c4_n64.md)
-    ("k_march", "fp64", "c4"): {"bytes_per_cell": 21669.0, "files": _MARCH_SRC,
-                                "digest": "1c7a3890492da430"},
+    ("k_march", "fp64", "c4"): {"bytes_per_cell": 21663.0, "files": _MARCH_SRC,
+                                "digest": "846f85d3c4e93627"},
 }
 
 
@@ -708,12 +718,14 @@ def main():
         rooflines["k_march"]["hbm"] = {
             "algorithmic_bytes": mbytes, "achieved_gbs": mbytes / (march_ms / 1e3) / 1e9,
             "peak_gbs": hbm_peak_m, "frac": mbytes / (march_ms / 1e3) / 1e9 / hbm_peak_m}
+    alu = int(main_opts.get("alu", 1))        # SMC_OPT_ALU (library default 1)
     n_fine = launches["fine"]
     if n_fine:
         per = rsub - 1
         fine_ms = kms["fine"] / n_fine
-        fl = fine_flops_per_substep(wl.mech.ns, wl.mech.nr, M1, rsub,
-                                    rates32=main_opts.get("rates", 0) == 1) * ncells * per
+        rates32 = main_opts.get("rates", 0) == 1
+        fl = fine_flops_per_substep(wl.mech.ns, wl.mech.nr, M1, rsub, rates32=rates32,
+                                    alu=alu) * ncells * per
         rooflines["k_fine_chain"] = {
             "bound": "alu", "kernel": "k_fine_chain (reaction substeps of one coarse interval)",
             "achieved": fl / (fine_ms / 1e3) / 1e12, "peak": fp64_peak / 1e12, "unit": "TFLOP/s",
@@ -721,10 +733,20 @@ def main():
             "traffic": ncu_traffic("k_fine_chain", main_key, args.workload, ncells),
             "peak_source": src64,
             "share": kms["fine"] / max(sum(kms.values()), 1e-9)}
+        if alu and not rates32:
+            # the same work counted as the FP64 operations of the FP64-pipe
+            # exponentials it replaces
+            fl_eq = fine_flops_per_substep(wl.mech.ns, wl.mech.nr, M1, rsub, alu=0) * ncells * per
+            rooflines["k_fine_chain"]["fp64_equivalent"] = {
+                "achieved": fl_eq / (fine_ms / 1e3) / 1e12,
+                "frac": fl_eq / (fine_ms / 1e3) / fp64_peak,
+                "note": "achieved/frac count the FP64-pipe flops; here the exponentials, which "
+                        "run on the integer and FP32 pipes, are counted as the 14 FP64 flops each "
+                        "they replace"}
     if launches.get("bdf"):
         bdf_ms = kms["bdf"] / launches["bdf"]
         evals_launch = R["bdf_evals"] / launches["bdf"]
-        fl = chem_flops_per_eval(wl.mech.ns, wl.mech.nr) * evals_launch
+        fl = chem_flops_per_eval(wl.mech.ns, wl.mech.nr, alu) * evals_launch
         rooflines["k_react_bdf"] = {
             "bound": "alu", "kernel": "k_react_bdf (implicit reactions over one coarse interval)",
             "achieved": fl / (bdf_ms / 1e3) / 1e12, "peak": fp64_peak / 1e12, "unit": "TFLOP/s",

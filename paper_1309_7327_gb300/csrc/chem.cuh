@@ -52,6 +52,18 @@ __device__ __forceinline__ double fast_exp(const Mech &m, double x) {
   return __hiloint2double(__double2hiint(y) + (k << 20), __double2loint(y));
 }
 
+// A float's value truncated toward zero to a 64-bit integer, in integer
+// arithmetic (a float-to-int64 conversion instruction would occupy the FP64
+// pipe); for |v| < 2^62.
+__device__ __forceinline__ long long float_to_ll(float v) {
+  const unsigned b = __float_as_uint(v);
+  const int e = (int)((b >> 23) & 0xff) - 150;          // v = m 2^e, m the 24-bit significand
+  const long long m = (long long)((b & 0x7fffffu) | 0x800000u);
+  long long r = 0;
+  if ((b & 0x7f800000u) != 0) r = e >= 0 ? (m << e) : (e > -24 ? (m >> -e) : 0);
+  return (b >> 31) ? -r : r;
+}
+
 // exp(x) to the accuracy of fast_exp without FP64 arithmetic on its main
 // path.  On this GPU the FP64 pipe issues one operation for every 64 of the
 // FP32 pipe, and exponentials are a third of the FP64 operations of the
@@ -125,7 +137,7 @@ __device__ __forceinline__ double exp_alu(const Mech &m, double x) {
   const float tl = (float)(unsigned)(MT & 0x1FFFFFFFULL) * 0x1p-52f;
   const float q1 = th * ph2;
   const float q2 = fmaf(th, ph2, -q1) + fmaf(th, pl2, tl * ph2);
-  const long long Y = (long long)(MT << 10) + __float2ll_rn(q1 * 0x1p62f) + __float2ll_rn(q2 * 0x1p62f);
+  const long long Y = (long long)(MT << 10) + float_to_ll(q1 * 0x1p62f) + float_to_ll(q2 * 0x1p62f);
   int sh = 10, eadj = 0;
   if (Y < (1LL << 62)) {
     sh = 9;

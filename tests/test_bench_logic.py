@@ -35,7 +35,9 @@ def test_traffic_table_names_existing_sources():
 def test_flop_counts_grow_with_the_mechanism():
     """Per reaction 34 and per species 43 FP64 flops in the rates; the line
     kernel's count is affine in the species count."""
-    assert bench.chem_flops_per_eval(21, 84) - bench.chem_flops_per_eval(21, 83) == 34.0
-    assert bench.chem_flops_per_eval(21, 84) - bench.chem_flops_per_eval(20, 84) == 43.0
+    assert bench.chem_flops_per_eval(21, 84, 0) - bench.chem_flops_per_eval(21, 83, 0) == 34.0
+    assert bench.chem_flops_per_eval(21, 84, 0) - bench.chem_flops_per_eval(20, 84, 0) == 43.0
+    # exponentials off the FP64 pipe: 14 flops less per reaction, species and cell
+    assert bench.chem_flops_per_eval(21, 84, 0) - bench.chem_flops_per_eval(21, 84, 1) == 14.0 * 106
     a, b, c = (bench.march_flops_per_cell(n) for n in (3, 9, 15))
     assert b - a == c - b > 0
