@@ -314,6 +314,30 @@ def _oracle_worker(job):
             return evals, el
 
 
+def _host_cpu() -> str:
+    """The host's architecture and CPU model (lscpu's, else /proc/cpuinfo's)."""
+    import platform
+    import subprocess
+    model = ""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    if not model:
+        try:
+            for line in open("/proc/cpuinfo"):
+                if line.lower().startswith(("model name", "cpu part")):
+                    model = line.split(":", 1)[1].strip()
+                    break
+        except OSError:
+            pass
+    return f"{platform.machine()} {model}".strip()
+
+
 def cpu_baseline(wl, budget_s: float = 15.0, all_cores_s: float = 0.0):
     """The oracle's right-hand side on a bounded sample of the workload's boxes
     (host cores, NumPy, single thread).  all_cores_s > 0: the same sample on
@@ -346,7 +370,7 @@ def cpu_baseline(wl, budget_s: float = 15.0, all_cores_s: float = 0.0):
         if el > budget_s or evals >= 50:
             break
     out = {"value": cells * evals / el / 1e6, "unit": "Mcell-RHS/s", "cores": 1,
-           "kind": "oracle",
+           "kind": "oracle", "host": _host_cpu(),
            "sample": f"{evals} full RHS evaluations of {cells} cells of box {b} of workload "
                      f"{wl.name} by the NumPy FP64 oracle, {el:.1f} s"}
     if all_cores_s > 0:
